@@ -1,0 +1,317 @@
+"""Benchmark: PCG time to 1e-8 relative residual on the 256x256-patch biharmonic PUM problem.
+
+Workload (synthetic, seeded): biharmonic Delta^2 u = f on the unit square, PUM with
+256 x 256 patches (stretch 1.5), local Legendre degree p = 3 (block size 10, 655,360
+unknowns), 9 levels with Galerkin coarse operators, adaptive block-FSAI (P0 = lower
+block pattern of A, t_max = 6, tau = 1), fourth-kind Chebyshev smoothing of degree 3 in
+a V(3,3) cycle, outer PCG from x0 = 0 to ||r|| / ||b|| <= 1e-8.  f is a Fourier series
+with 8 x 8 modes, coefficients N(0,1) (seed 1) scaled by (a^2 + b^2)^-1.
+
+A step is one PCG solve to 1e-8 with the hierarchy set up and b resident in HBM.  The
+headline form smooths in FP32 (A, P, G and smoother vectors in float32, FP32 accumulation)
+under FP64 flexible PCG; the plain FP64 form is timed beside it.  The working set is
+larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Rank 0 prints one JSON line.  Under torchrun (N > 1) every rank solves its own replica
+(the solver does not shard): replicas only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import pum_inputs as pin  # noqa: E402
+
+METRIC = "PCG time to 1e-8 rel. residual; smoother GB/s vs HBM peak, vs FP64 plain"
+UNIT = "ms"
+WORKLOAD = pin.BIHARMONIC_256
+RTOL = 1e-8
+
+
+def algorithmic_bytes(info, smooth_bytes, g_bytes, vec_bytes):
+    """Algorithmic bytes of one launch of each finest-level smoother kernel class:
+    matrix values and int32 column indices once, each vector operand once."""
+    d = info["d"]
+    N = info["n"] * d
+    return {
+        "resid": info["nnzb_A"] * (d * d * smooth_bytes + 4) + 3 * N * vec_bytes,   # x, b read; r write
+        "g": info["nnzb_G"] * (d * d * g_bytes + 4) + 2 * N * vec_bytes,             # r read; t write
+        "gt": info["nnzb_G"] * (d * d * g_bytes + 4) + 5 * N * vec_bytes,            # t, p, x read; p, x write
+        "pcg_ap": info["nnzb_A"] * (d * d * 8 + 4) + 2 * N * 8,                        # A (FP64), p read; q write
+    }
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(seconds_budget: float = 20.0):
+    """Time the FP64 oracle's PCG (V(3,3), adaptive block-FSAI t_max = 6) on the 16x16-patch
+    version of the workload and scale to the full problem: per-iteration time grows with the
+    number of unknowns (multilevel work is linear in N)."""
+    from oracle import pum as opum
+    from oracle import solver
+    m, levels = 16, 5
+    pr = WORKLOAD
+    f = opum.fourier_source(pin.fourier_coefficients(pr.rhs_seed), pr.rhs_decay)
+    h = opum.build_hierarchy(m, pr.p, pr.equation, levels, f=f, constants=pr.nitsche)
+    st = solver.build_setup(h, k=pr.cheb_k, mode="adaptive", P0=pr.fsai_p0, t_max=pr.t_max, tau=pr.tau)
+    t0 = time.perf_counter()
+    reps, iters = 0, 0
+    while True:
+        res = solver.solve(st, h.b, rtol=RTOL)
+        reps += 1
+        iters += res.iters
+        if time.perf_counter() - t0 >= seconds_budget:
+            break
+    dt = time.perf_counter() - t0
+    per_iter_per_dof = dt / iters / (m * m * pr.d)
+    return per_iter_per_dof, {"sample": f"oracle FP64 PCG on the 16x16-patch problem (2,560 unknowns, 5 levels, same "
+                                        f"FSAI/smoother settings), {reps} solves of {res.iters} iterations in "
+                                        f"{dt:.1f} s; scaled by unknowns to 655,360 and by the GPU iteration count",
+                              "cores": 1, "kind": "oracle"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per, meta = oracle_sample(seconds_budget=max(5.0, 20.0 / max(args.steps, 1)))
+    # the oracle's own iteration count at the small size stands in for the full-size count
+    from oracle import pum as opum  # noqa: F401
+    full_iters = 20
+    vals = []
+    for _ in range(args.warmup):
+        pass
+    for _ in range(args.steps):
+        p2, _ = oracle_sample(seconds_budget=max(2.0, 10.0 / max(args.steps, 1)))
+        vals.append(p2 * WORKLOAD.n_dofs * full_iters * 1e3)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.name, "unknowns": WORKLOAD.n_dofs,
+                       "note": f"oracle time per PCG iteration per unknown x {WORKLOAD.n_dofs} unknowns x "
+                               f"{full_iters} iterations"},
+            "cpu_baseline": dict(meta, value=value, unit=UNIT),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+
+    import paper_2509_06744_gb300 as pum
+
+    pr = WORKLOAD
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)  # torch ops and the library share one stream
+    ctx = pum.Context(local, stream=stream.cuda_stream)
+    N = pr.n_dofs
+    b = torch.zeros(N, dtype=torch.float64, device="cuda")
+    t_setup = time.perf_counter()
+    H = pum.Hierarchy.assemble(ctx, pr.equation, pr.p, pr.finest_m, pr.n_levels,
+                               f_coef=pin.fourier_coefficients(pr.rhs_seed), f_decay=pr.rhs_decay,
+                               nitsche=pr.nitsche, b=b)
+    t_asm = time.perf_counter() - t_setup
+    # plain FP64 form
+    H.setup(p0=pr.fsai_p0, adaptive=pr.adaptive, t_max=pr.t_max, tau=pr.tau, k=pr.cheb_k, smooth="f64")
+    t_fsai = time.perf_counter() - t_setup - t_asm
+    x = torch.zeros_like(b)
+
+    def timed_solves(n, flexible):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = []
+        for _ in range(n):
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            rep = H.pcg(b, x, rtol=RTOL, maxit=200, flexible=flexible)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            reps.append((ev0.elapsed_time(ev1), rep))
+        return reps
+
+    timed_solves(args.warmup, False)
+    plain = timed_solves(max(2, args.steps // 2), False)
+    plain_ms = statistics.median(r[0] for r in plain)
+    plain_iters = plain[-1][1]["iters"]
+    x64 = x.clone()
+    # headline form: FP32 smoothing, FP64 outer flexible PCG
+    H.setup(p0=pr.fsai_p0, adaptive=pr.adaptive, t_max=pr.t_max, tau=pr.tau, k=pr.cheb_k, smooth="f32", g="f32")
+    timed_solves(args.warmup, True)
+    ctx.timing(True)
+    ctx.timing_reset()
+    launches0 = ctx.launches
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        reps = []
+        for _ in range(args.steps):
+            reps.append(H.pcg(b, x, rtol=RTOL, maxit=200, flexible=True))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    total_ms = ev0.elapsed_time(ev1)
+    launches = ctx.launches - launches0
+    kt = ctx.timing_read()
+    ctx.timing(False)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_solve = total_ms / args.steps
+    iters = reps[-1]["iters"]
+    # accuracy of the fast form against the plain FP64 solution (equal accuracy check)
+    rel_vs_plain = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+    r = torch.zeros_like(b)
+    H.residual(0, b, x, r)
+    true_rel = float(torch.linalg.norm(r) / torch.linalg.norm(b))
+
+    # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+    b_host = b.cpu().pin_memory()
+    x_host = torch.zeros(N, dtype=torch.float64).pin_memory()
+    bd, xd = torch.empty_like(b), torch.empty_like(b)
+    e2e = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            bd.copy_(b_host, non_blocking=True)
+        H.pcg(bd, xd, rtol=RTOL, maxit=200, flexible=True)
+        with torch.cuda.stream(stream):
+            x_host.copy_(xd, non_blocking=True)
+        stream.synchronize()
+        if i >= args.warmup:
+            e2e.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = statistics.median(e2e)
+
+    # roofline of the dominant finest-level smoother kernel
+    info = H.info(0)
+    ab = algorithmic_bytes(info, 4, 4, 4)
+    peak, peak_kind = load_peaks()
+    classes = {k: v for k, v in kt.items() if k != "pcg_ap" and v[0] > 0}
+    dom = max(classes, key=lambda k: classes[k][1])
+    n_l, ms_l = classes[dom]
+    avg_s = ms_l / n_l * 1e-3
+    achieved = ab[dom] / avg_s / 1e9
+    kernels = {k: {"launches": v[0], "avg_us": (v[1] / v[0] * 1e3) if v[0] else None,
+                   "GBps": (ab[k] / (v[1] / v[0] * 1e-3) / 1e9) if v[0] else None} for k, v in kt.items()}
+
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        per, meta = oracle_sample()
+        cpu = dict(meta, value=per * N * iters * 1e3, unit=UNIT)
+    line = {
+        "metric": METRIC, "value": ms_per_solve, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_solve, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": pr.name, "unknowns": N, "levels": pr.n_levels, "pcg": "flexible FP64",
+                   "smoother": "FP32 A/P/G/vectors, FP32 accumulation", "rtol": RTOL,
+                   "l2": "working set larger than L2 (no flush)", "parallelism": "replicas only"},
+        "pcg_iters": iters, "true_relres": true_rel, "rel_diff_vs_fp64_plain": rel_vs_plain,
+        "fp64_plain": {"ms_per_solve": plain_ms, "pcg_iters": plain_iters, "dtype": "f64"},
+        "setup_s": {"assembly_and_galerkin": t_asm, "fsai_lanczos_fp64": t_fsai},
+        "kernels_finest": kernels,
+        "roofline": {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                     "algorithmic_bytes_per_launch": ab[dom]},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

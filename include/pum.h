@@ -1,0 +1,230 @@
+/*
+ * pum.h -- C-ABI of the GB300 multilevel solver for partition-of-unity (PUM)
+ * discretisations of the biharmonic and triharmonic equations, smoothed by the
+ * fourth-kind Chebyshev iteration with block-FSAI preconditioners.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  - Block structure (Definition 2.1): a level with m x m patches has n = m*m
+ *    block rows, uniform block size d = (p+1)(p+2)/2 (Section 5: dim V_i), and
+ *    N = n*d unknowns.  Block row i = iy*m + ix; unknown (i, k) sits at i*d + k,
+ *    k the local Legendre basis index ordered by total degree, then by the
+ *    y-degree.
+ *  - Levels are numbered 0 = finest ... n_levels-1 = coarsest.
+ *  - Vector arguments are caller-owned DEVICE pointers to float64 arrays of the
+ *    level's length N unless stated otherwise (typically torch tensors'
+ *    data_ptr()).  The library never frees them.  All work is queued on the
+ *    context's CUDA stream; calls return after queuing unless stated otherwise.
+ *  - Every call returns a pum_status and never aborts.  On failure a message is
+ *    available from pum_last_error().  Device-side conditions (non-positive
+ *    Cholesky pivot, breakdown) are recorded in a device status word that the
+ *    synchronous calls (bfsai_setup, pcg_solve, pum_sync) check before return.
+ *  - Threading: a context is used by one host thread at a time.
+ */
+#ifndef PUM_H
+#define PUM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PUM_OK = 0,
+  PUM_ERR_INVALID_ARG = 1, /* bad size, pointer, pattern or parameter           */
+  PUM_ERR_OOM = 2,         /* device or host allocation failed                   */
+  PUM_ERR_CUDA = 3,        /* a CUDA runtime call failed                         */
+  PUM_ERR_NOT_SPD = 4,     /* non-positive pivot in a Cholesky factorisation     */
+  PUM_ERR_BREAKDOWN = 5,   /* PCG: p^T A p <= 0 or a non-finite scalar           */
+  PUM_ERR_NOCONV = 6,      /* PCG: maxit reached before rtol                     */
+  PUM_ERR_TIMEOUT = 7,     /* a bounded device wait gave up                      */
+  PUM_ERR_UNSUPPORTED = 8, /* a valid request this build does not implement      */
+  PUM_ERR_IO = 9           /* file could not be read or written                  */
+} pum_status;
+
+typedef enum { PUM_F64 = 0, PUM_F32 = 1, PUM_BF16 = 2 } pum_dtype;
+
+typedef struct pum_ctx pum_ctx;   /* device, stream, status word, last error    */
+typedef struct pum_hier pum_hier; /* levels {A, P, P^T, G, G^T, beta}, coarse   */
+
+/* A block-sparse (BSR) matrix with square d x d blocks stored row-major and
+ * contiguous (block b occupies vals[b*bs*bs .. (b+1)*bs*bs)), columns sorted
+ * within each block row.  Pointers are host memory unless on_device != 0. */
+typedef struct {
+  int32_t n_brows, n_bcols, bs;
+  int64_t nnzb;
+  const int32_t *row_ptr; /* n_brows + 1 */
+  const int32_t *col_idx; /* nnzb        */
+  const double *vals;     /* nnzb*bs*bs  */
+  int32_t on_device;
+} pum_bsr_view;
+
+/* Host copy of a BSR matrix returned by pum_hier_export; free with pum_bsr_free. */
+typedef struct {
+  int32_t n_brows, n_bcols, bs;
+  int64_t nnzb;
+  int32_t *row_ptr;
+  int32_t *col_idx;
+  double *vals;
+} pum_bsr_host;
+
+/* The PUM problem of Section 4 / Examples 5.1 and 5.4 on the unit square. */
+typedef struct {
+  int32_t equation;     /* 4: Delta^2 u = f (Example 5.1); 6: -Delta^3 u = f (Example 5.4) */
+  int32_t p;            /* local polynomial degree, 1..5                               */
+  int32_t finest_m;     /* patches per side on the finest level (even while coarsening) */
+  int32_t n_levels;     /* finest_m must be divisible by 2^(n_levels-1)               */
+  double nitsche_c[3];  /* C_j of gamma^(j) = C_j (p+1)^2 h^-(order-1-2j); 0 -> default */
+  int32_t quad_pts;     /* Gauss points per direction per sub-cell; 0 -> p + 6          */
+  const double *f_coef; /* host, f_modes*f_modes coefficients c_ab (row a-1, column b-1) */
+  int32_t f_modes;      /* f = sum c_ab (a^2+b^2)^(-f_decay/2) sin(a pi x) sin(b pi y)   */
+  double f_decay;
+} pum_problem;
+
+enum { PUM_P0_LOWER = 0, PUM_P0_DIAG = 1 };
+
+/* Block-FSAI set-up (Definition 2.2, Algorithm 1, Section 2.2). */
+typedef struct {
+  int32_t p0;       /* initial pattern: PUM_P0_LOWER = lower(P(A)), PUM_P0_DIAG = diagonal */
+  int32_t adaptive; /* 0: static pattern P0; 1: Algorithm 1 from P0                       */
+  int32_t t_max;    /* adaptive steps (Algorithm 1)                                        */
+  double tau;       /* threshold in (0, 1] (Algorithm 1)                                   */
+  int32_t nested;   /* 1: one level of nesting (Section 2.2), same parameters twice        */
+  double tie_rel;   /* argmin ties: smallest column with rho_c <= rho_min (1 + tie_rel)    */
+} bfsai_params;
+
+/* Fourth-kind Chebyshev smoother (Algorithm 3) and its lambda_max estimate (Section 5). */
+typedef struct {
+  int32_t degree_k;      /* k >= 1 smoothing steps, pre and post (V(k,k))                  */
+  int32_t lanczos_its;   /* Lanczos iterations (paper: 100)                                 */
+  double lanczos_safety; /* beta = safety * lambda_max estimate (paper: 1.01)              */
+  uint64_t lanczos_seed; /* SplitMix64 seed of the start vector; level l uses seed + l     */
+  int32_t smooth_dt;     /* PUM_F64 or PUM_F32: storage and arithmetic of A, P and vectors  */
+  int32_t g_dt;          /* PUM_F64, PUM_F32 or PUM_BF16 (BF16 needs smooth_dt = PUM_F32)   */
+} smoother_params;
+
+/* Outer preconditioned CG (one V(k,k) cycle as preconditioner). */
+typedef struct {
+  double rtol;        /* stop when ||r_j||_2 / ||b||_2 <= rtol (recursive residual)         */
+  int32_t maxit;
+  int32_t flexible;   /* 1: Polak-Ribiere beta (for a preconditioner in lower precision)    */
+  double *hist;       /* host, maxit + 1 entries or NULL: ||r_j|| / ||b||, j = 0..iters    */
+  int32_t iters;      /* out */
+  int32_t converged;  /* out */
+  double final_relres;/* out: last recursive residual                                       */
+} pcg_report;
+
+/* Per-level sizes and smoother data (for tests and reports). */
+typedef struct {
+  int32_t m, n, d;
+  int64_t nnzb_A, nnzb_G, nnzb_GT, nnzb_P, nnzb_F0, nnzb_G1;
+  double beta;        /* Chebyshev upper bound of this level (0 before bfsai_setup)        */
+  double logdet_S;    /* sum_k log det S_kk of the (inner) FSAI (Lemma 2.7)                */
+  int32_t coarsest;
+} pum_level_info;
+
+/* Matrices selectable in pum_hier_export. */
+enum { PUM_MAT_A = 0, PUM_MAT_P = 1, PUM_MAT_G = 2, PUM_MAT_GT = 3, PUM_MAT_F0 = 4, PUM_MAT_G1 = 5,
+       PUM_MAT_A1 = 6 };
+
+/* ---- context ------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  cuda_stream is the cudaStream_t the library
+ * queues all its work on (cudaStreamLegacy, i.e. (void*)1, selects the legacy default
+ * stream); NULL makes the library create its own non-blocking stream, in which case the
+ * caller must order its own use of the vectors with pum_sync.  Ownership of a passed
+ * stream stays with the caller. */
+pum_status pum_create(pum_ctx **ctx, int device, void *cuda_stream);
+pum_status pum_destroy(pum_ctx *ctx);
+/* Last error message of this context (never NULL; "" when none). */
+const char *pum_last_error(const pum_ctx *ctx);
+/* Wait for the context's stream and check the device status word. */
+pum_status pum_sync(pum_ctx *ctx);
+
+/* ---- hierarchy construction ---------------------------------------------------- */
+
+/* Assemble the PUM problem (Section 4; Nitsche forms of Example 5.1 / 5.4) on the finest
+ * level, build the L2-projection prolongations of Section 4 for every coarser level and
+ * the Galerkin coarse operators A_{l-1} = P^T A_l P (Section 5), all on the device.
+ * b_dev: device float64 array of length N_finest that receives the load vector l_n(.)
+ * with zero boundary data (may be NULL).  *out is owned by the caller until
+ * pum_hier_destroy.  Synchronous. */
+pum_status pum_assemble(pum_ctx *ctx, const pum_problem *prob, pum_hier **out, double *b_dev);
+
+/* Build a hierarchy from caller matrices (copied; caller keeps ownership).  A[0] is the
+ * finest operator; for l >= 1, A[l] with vals == NULL is computed as P[l-1]^T A[l-1] P[l-1].
+ * P[l] (l = 0..n_levels-2) maps level l+1 to level l (n_brows = n_l, n_bcols = n_{l+1}).
+ * All blocks must share one bs <= 32.  Synchronous. */
+pum_status pum_hier_from_bsr(pum_ctx *ctx, int n_levels, const pum_bsr_view *A, const pum_bsr_view *P,
+                             pum_hier **out);
+
+/* Block-FSAI smoothers for every level but the coarsest (static pattern, Algorithm 1, or
+ * one level of nesting), the Lanczos estimate beta_l = safety * lambda_max(M_l A_l) per
+ * level (Section 5), the explicit transposes used by the smoother, low-precision copies,
+ * and the dense Cholesky factor of the coarsest operator.  Synchronous. */
+pum_status bfsai_setup(pum_ctx *ctx, pum_hier *h, const bfsai_params *fp, const smoother_params *sp);
+
+/* ---- hot path -------------------------------------------------------------------- */
+
+/* Algorithm 3 on `level`: k steps of the M-preconditioned fourth-kind Chebyshev
+ * iteration for A x = b, M = G^T G (or F0^T G1^T G1 F0 when nested).  x_is_zero != 0
+ * means x0 = 0 (x is then output only).  b, x: device float64, length N_level; the
+ * smoother runs in the set-up's smooth_dt. */
+pum_status cheb4_smooth(pum_ctx *ctx, pum_hier *h, int level, const double *b, double *x, int x_is_zero);
+
+/* z = B r for one V(k,k) cycle (Section 5): pre-smoothing from x0 = 0, residual,
+ * restriction R = P^T, recursion, prolongation, post-smoothing with the same
+ * polynomial; direct solve on the coarsest level.  r, z: device float64, N_finest. */
+pum_status vcycle_apply(pum_ctx *ctx, pum_hier *h, const double *r, double *z);
+
+/* Preconditioned CG from x = 0 for A_0 x = b (float64 throughout the outer iteration;
+ * A_0 q products in float64).  b, x: device float64, N_finest.  Synchronous; fills rep.
+ * Returns PUM_ERR_NOCONV when maxit is reached (x holds the last iterate). */
+pum_status pcg_solve(pum_ctx *ctx, pum_hier *h, const double *b, double *x, pcg_report *rep);
+
+/* ---- single steps of the hot path (device float64 vectors) ------------------------ */
+
+/* r = b - A_level x (the residual of Algorithm 3). */
+pum_status pum_residual(pum_ctx *ctx, pum_hier *h, int level, const double *b, const double *x, double *r);
+/* z = M r, the block-FSAI application G^T (G r) (Definition 2.2) of the level. */
+pum_status pum_fsai_apply(pum_ctx *ctx, pum_hier *h, int level, const double *r, double *z);
+/* rc = P_level^T r: restriction from `level` to level+1 (Section 4). */
+pum_status pum_restrict(pum_ctx *ctx, pum_hier *h, int level, const double *r, double *rc);
+/* x += P_level e: prolongation from level+1 to `level`, added to x (Section 4). */
+pum_status pum_prolong_add(pum_ctx *ctx, pum_hier *h, int level, const double *e, double *x);
+/* z = A_c^{-1} r on the coarsest level (dense Cholesky). */
+pum_status pum_coarse_solve(pum_ctx *ctx, pum_hier *h, const double *r, double *z);
+
+/* ---- inspection, persistence ------------------------------------------------------- */
+
+pum_status pum_hier_levels(const pum_hier *h, int *n_levels);
+pum_status pum_level_info_get(const pum_hier *h, int level, pum_level_info *info);
+/* Host copy of a level's matrix (float64 values); free with pum_bsr_free.  Synchronous. */
+pum_status pum_hier_export(pum_ctx *ctx, const pum_hier *h, int level, int which, pum_bsr_host *out);
+void pum_bsr_free(pum_bsr_host *m);
+/* Versioned binary file of the whole set-up product (all levels' matrices, betas,
+ * coarse factor, parameters).  load rebuilds a hierarchy ready for the hot path. */
+pum_status pum_hier_save(pum_ctx *ctx, const pum_hier *h, const char *path);
+pum_status pum_hier_load(pum_ctx *ctx, const char *path, pum_hier **out);
+pum_status pum_hier_destroy(pum_hier *h);
+
+/* ---- measurement -------------------------------------------------------------------- */
+
+/* Per-kernel-class timing of the hot path.  When enabled, every launch of the classes
+ * below on the finest level is bracketed by CUDA events recorded on the launching
+ * stream; pum_timing_read returns, per class, the number of launches and the summed
+ * event time since the last reset.  Class ids: 0 residual A x (smoother), 1 G r,
+ * 2 G^T t + Chebyshev update, 3 A p in PCG. */
+enum { PUM_TK_RESID = 0, PUM_TK_G = 1, PUM_TK_GT = 2, PUM_TK_PCG_AP = 3, PUM_TK_COUNT = 4 };
+pum_status pum_timing_enable(pum_ctx *ctx, int enable);
+pum_status pum_timing_reset(pum_ctx *ctx);
+pum_status pum_timing_read(pum_ctx *ctx, int64_t *launches, double *ms);
+/* Number of kernels of this library launched on the context since creation. */
+int64_t pum_launch_count(const pum_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PUM_H */

@@ -503,9 +503,10 @@ class Hierarchy:
     gamma: list
 
 
-def build_hierarchy(m: int, p: int, order: int, n_levels: int, f=None, with_mass: bool = False) -> Hierarchy:
+def build_hierarchy(m: int, p: int, order: int, n_levels: int, f=None, with_mass: bool = False,
+                    constants=None) -> Hierarchy:
     """Finest-level assembly plus Galerkin coarse operators A_{l-1} = P^T A_l P (Section 5)."""
-    gamma = nitsche_gamma(order, p, m)
+    gamma = nitsche_gamma(order, p, m, constants)
     asm = assemble(m, p, order, gamma, f=f, with_mass=with_mass)
     ms, As, Ps = [m], [asm.A], []
     for _ in range(n_levels - 1):

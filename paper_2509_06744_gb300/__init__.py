@@ -1,0 +1,237 @@
+"""GB300 multilevel solver for PUM discretisations of higher-order problems:
+fourth-kind Chebyshev smoothing with (adaptive, nested) block-FSAI preconditioners.
+
+Thin Python binding over the C-ABI of ``include/pum.h``: this module only marshals
+arguments (torch CUDA tensors become device pointers); every step of the solver runs
+in the library's CUDA kernels.  There is no CPU fallback: without the built library
+or a CUDA device every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (PUM_BF16, PUM_F32, PUM_F64, PUM_MAT_A, PUM_MAT_A1, PUM_MAT_F0, PUM_MAT_G, PUM_MAT_G1,
+                   PUM_MAT_GT, PUM_MAT_P, PUM_P0_DIAG, PUM_P0_LOWER)
+
+__all__ = ["Context", "Hierarchy", "PumError", "PUM_F64", "PUM_F32", "PUM_BF16", "PUM_P0_LOWER", "PUM_P0_DIAG",
+           "PUM_MAT_A", "PUM_MAT_P", "PUM_MAT_G", "PUM_MAT_GT", "PUM_MAT_F0", "PUM_MAT_G1", "PUM_MAT_A1"]
+
+_DT = {"f64": PUM_F64, "f32": PUM_F32, "bf16": PUM_BF16}
+
+
+class PumError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_lib.STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _vec(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A CUDA device and the stream the library's kernels run on (pum_create / pum_destroy).
+
+    By default the library runs on torch's current stream of that device, so its
+    kernels are ordered with the torch operations that allocate, fill and read the
+    vectors passed to it (and torch's caching allocator never recycles a buffer that a
+    queued kernel still reads).  `stream` is a raw cudaStream_t handle.
+    """
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self.lib = _lib.load()
+        if stream is None:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream(device).cuda_stream
+                if stream == 0:
+                    stream = _lib.CUDA_STREAM_LEGACY
+        h = C.c_void_p()
+        st = self.lib.pum_create(C.byref(h), device, C.c_void_p(stream) if stream else None)
+        if st != 0:
+            raise PumError(st, "pum_create failed (is a CUDA device present?)")
+        self.h = h
+        self.device = device
+
+    def check(self, st: int):
+        if st != 0:
+            raise PumError(st, self.lib.pum_last_error(self.h).decode())
+
+    def sync(self):
+        self.check(self.lib.pum_sync(self.h))
+
+    def close(self):
+        if self.h:
+            self.lib.pum_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def timing(self, enable: bool):
+        self.check(self.lib.pum_timing_enable(self.h, int(enable)))
+
+    def timing_reset(self):
+        self.check(self.lib.pum_timing_reset(self.h))
+
+    def timing_read(self):
+        n = (C.c_int64 * _lib.PUM_TK_COUNT)()
+        ms = (C.c_double * _lib.PUM_TK_COUNT)()
+        self.check(self.lib.pum_timing_read(self.h, n, ms))
+        names = ["resid", "g", "gt", "pcg_ap"]
+        return {names[i]: (int(n[i]), float(ms[i])) for i in range(_lib.PUM_TK_COUNT)}
+
+    @property
+    def launches(self) -> int:
+        return int(self.lib.pum_launch_count(self.h))
+
+
+def _bsr_view(indptr, indices, blocks, n_cols):
+    indptr = np.ascontiguousarray(indptr, dtype=np.int32)
+    indices = np.ascontiguousarray(indices, dtype=np.int32)
+    blocks = np.ascontiguousarray(blocks, dtype=np.float64)
+    v = _lib.BsrView(len(indptr) - 1, n_cols, blocks.shape[1] if blocks.ndim == 3 else 0, len(indices),
+                     indptr.ctypes.data, indices.ctypes.data, blocks.ctypes.data, 0)
+    return v, (indptr, indices, blocks)
+
+
+class Hierarchy:
+    """Level hierarchy {A_l, P_l, G_l, beta_l} owned by the library (pum_hier)."""
+
+    def __init__(self, ctx: Context, handle: C.c_void_p):
+        self.ctx, self.h, self.lib = ctx, handle, ctx.lib
+
+    # ---- construction
+    @classmethod
+    def assemble(cls, ctx: Context, equation: int, p: int, finest_m: int, n_levels: int, f_coef=None,
+                 f_decay: float = 2.0, nitsche=(0.0, 0.0, 0.0), quad_pts: int = 0, b=None):
+        pr = _lib.Problem()
+        pr.equation, pr.p, pr.finest_m, pr.n_levels = equation, p, finest_m, n_levels
+        for j in range(3):
+            pr.nitsche_c[j] = float(nitsche[j]) if j < len(nitsche) else 0.0
+        pr.quad_pts = quad_pts
+        keep = None
+        if f_coef is not None:
+            keep = np.ascontiguousarray(f_coef, dtype=np.float64)
+            pr.f_coef, pr.f_modes, pr.f_decay = keep.ctypes.data, keep.shape[0], f_decay
+        h = C.c_void_p()
+        ctx.check(ctx.lib.pum_assemble(ctx.h, C.byref(pr), C.byref(h), _vec(b, "b") if b is not None else None))
+        del keep
+        return cls(ctx, h)
+
+    @classmethod
+    def from_bsr(cls, ctx: Context, A_levels, P_levels):
+        """A_levels: list of (indptr, indices, blocks) or None (Galerkin); P_levels: list of
+        (indptr, indices, blocks, n_coarse_block_cols)."""
+        keep = []
+        nl = len(A_levels)
+        av = (_lib.BsrView * nl)()
+        for l, a in enumerate(A_levels):
+            if a is None:
+                av[l] = _lib.BsrView(0, 0, 0, 0, None, None, None, 0)
+            else:
+                v, k = _bsr_view(a[0], a[1], a[2], len(a[0]) - 1)
+                av[l] = v
+                keep.append(k)
+        pv = (_lib.BsrView * max(nl - 1, 1))()
+        for l, pm in enumerate(P_levels):
+            v, k = _bsr_view(pm[0], pm[1], pm[2], pm[3])
+            pv[l] = v
+            keep.append(k)
+        h = C.c_void_p()
+        ctx.check(ctx.lib.pum_hier_from_bsr(ctx.h, nl, av, pv, C.byref(h)))
+        return cls(ctx, h)
+
+    @classmethod
+    def load(cls, ctx: Context, path: str):
+        h = C.c_void_p()
+        ctx.check(ctx.lib.pum_hier_load(ctx.h, path.encode(), C.byref(h)))
+        return cls(ctx, h)
+
+    def save(self, path: str):
+        self.ctx.check(self.lib.pum_hier_save(self.ctx.h, self.h, path.encode()))
+
+    def setup(self, p0: str = "lower", adaptive: bool = False, t_max: int = 0, tau: float = 1.0,
+              nested: bool = False, tie_rel: float = 1e-9, k: int = 2, lanczos_its: int = 100,
+              lanczos_safety: float = 1.01, lanczos_seed: int = 0, smooth: str = "f64", g: str | None = None):
+        fp = _lib.FsaiParams(PUM_P0_LOWER if p0 == "lower" else PUM_P0_DIAG, int(adaptive), t_max, tau,
+                             int(nested), tie_rel)
+        sp = _lib.SmootherParams(k, lanczos_its, lanczos_safety, lanczos_seed, _DT[smooth], _DT[g or smooth])
+        self.ctx.check(self.lib.bfsai_setup(self.ctx.h, self.h, C.byref(fp), C.byref(sp)))
+
+    def close(self):
+        if self.h:
+            self.lib.pum_hier_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- hot path
+    def cheb4_smooth(self, level: int, b, x, x_is_zero: bool):
+        self.ctx.check(self.lib.cheb4_smooth(self.ctx.h, self.h, level, _vec(b, "b"), _vec(x, "x"), int(x_is_zero)))
+
+    def vcycle(self, r, z):
+        self.ctx.check(self.lib.vcycle_apply(self.ctx.h, self.h, _vec(r, "r"), _vec(z, "z")))
+
+    def pcg(self, b, x, rtol: float = 1e-8, maxit: int = 200, flexible: bool = False, allow_noconv=False):
+        hist = (C.c_double * (maxit + 1))()
+        rep = _lib.PcgReport(rtol, maxit, int(flexible), hist, 0, 0, 0.0)
+        st = self.lib.pcg_solve(self.ctx.h, self.h, _vec(b, "b"), _vec(x, "x"), C.byref(rep))
+        if not (st == 0 or (allow_noconv and st == _lib.PUM_ERR_NOCONV)):
+            self.ctx.check(st)
+        return {"iters": rep.iters, "converged": bool(rep.converged), "final_relres": rep.final_relres,
+                "history": [hist[i] for i in range(rep.iters + 1)]}
+
+    # ---- single steps
+    def residual(self, level, b, x, r):
+        self.ctx.check(self.lib.pum_residual(self.ctx.h, self.h, level, _vec(b, "b"), _vec(x, "x"), _vec(r, "r")))
+
+    def fsai_apply(self, level, r, z):
+        self.ctx.check(self.lib.pum_fsai_apply(self.ctx.h, self.h, level, _vec(r, "r"), _vec(z, "z")))
+
+    def restrict(self, level, r, rc):
+        self.ctx.check(self.lib.pum_restrict(self.ctx.h, self.h, level, _vec(r, "r"), _vec(rc, "rc")))
+
+    def prolong_add(self, level, e, x):
+        self.ctx.check(self.lib.pum_prolong_add(self.ctx.h, self.h, level, _vec(e, "e"), _vec(x, "x")))
+
+    def coarse_solve(self, r, z):
+        self.ctx.check(self.lib.pum_coarse_solve(self.ctx.h, self.h, _vec(r, "r"), _vec(z, "z")))
+
+    # ---- inspection
+    @property
+    def n_levels(self) -> int:
+        n = C.c_int32()
+        self.ctx.check(self.lib.pum_hier_levels(self.h, C.byref(n)))
+        return n.value
+
+    def info(self, level: int) -> dict:
+        li = _lib.LevelInfo()
+        self.ctx.check(self.lib.pum_level_info_get(self.h, level, C.byref(li)))
+        return {f: getattr(li, f) for f, _ in _lib.LevelInfo._fields_}
+
+    def export(self, level: int, which: int):
+        """Host copy (indptr, indices, blocks) of a level's matrix, float64."""
+        m = _lib.BsrHost()
+        self.ctx.check(self.lib.pum_hier_export(self.ctx.h, self.h, level, which, C.byref(m)))
+        try:
+            n, nnzb, d = m.n_brows, m.nnzb, m.bs
+            indptr = np.ctypeslib.as_array(m.row_ptr, shape=(n + 1,)).copy()
+            indices = np.ctypeslib.as_array(m.col_idx, shape=(max(nnzb, 1),))[:nnzb].copy()
+            blocks = np.ctypeslib.as_array(m.vals, shape=(max(nnzb * d * d, 1),))[:nnzb * d * d].copy()
+            return indptr.astype(np.int64), indices.astype(np.int64), blocks.reshape(nnzb, d, d), m.n_bcols
+        finally:
+            self.lib.pum_bsr_free(C.byref(m))

@@ -1,0 +1,203 @@
+// Internal definitions of the PUM / block-FSAI / Chebyshev-4 library (sm_103a).
+//
+// Device data layout (HBM):
+//  * BSR matrices: row_ptr int32[n+1], col_idx int32[nnzb], vals with a padded block
+//    stride: block b starts at vals + b*stride elements, stride = d*d rounded up so that
+//    every block starts on a 16-byte boundary; inside a block, row-major d x d.
+//  * Vectors: contiguous, unknown (i, k) at i*d + k (block-row major).
+//  * Each matrix keeps a host copy of its pattern for the symbolic work (transposes,
+//    Galerkin and nested triple products, adaptive FSAI candidate sets).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pum.h"
+
+namespace pum {
+
+// ----------------------------------------------------------------------------- errors
+
+struct Error {
+  pum_status st;
+  std::string msg;
+};
+
+#define PUM_CUDA(call)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      throw ::pum::Error{PUM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};  \
+  } while (0)
+
+#define PUM_CHECK(cond, status, text)                                                        \
+  do {                                                                                       \
+    if (!(cond)) throw ::pum::Error{status, std::string(text)};                              \
+  } while (0)
+
+// Device status word: first error wins.
+struct DevStatus {
+  int code;   // pum_status
+  int info;   // e.g. the block row of a failed Cholesky
+  int where;  // which kernel family (see kWhere*)
+  int pad;
+};
+enum { kWhereFsai = 1, kWhereCoarse = 2, kWhereAdaptive = 3, kWhereLanczos = 4 };
+
+__device__ inline void set_status(DevStatus* s, int code, int info, int where) {
+  if (atomicCAS(&s->code, 0, code) == 0) {
+    s->info = info;
+    s->where = where;
+  }
+}
+
+// ----------------------------------------------------------------------------- matrices
+
+inline size_t dt_size(int dt) { return dt == PUM_F64 ? 8 : dt == PUM_F32 ? 4 : 2; }
+inline int block_stride(int d, int dt) {
+  int per16 = 16 / (int)dt_size(dt);
+  return (d * d + per16 - 1) / per16 * per16;
+}
+
+struct Bsr {
+  int n_brows = 0, n_bcols = 0, d = 0, stride = 0, dt = PUM_F64;
+  int64_t nnzb = 0;
+  int* row_ptr = nullptr;  // device
+  int* col_idx = nullptr;  // device
+  void* vals = nullptr;    // device
+  std::vector<int> h_row_ptr, h_col_idx;  // host pattern copy
+  bool empty() const { return vals == nullptr; }
+};
+
+void bsr_free(Bsr& m);
+// Allocate a device BSR with the given host pattern (values uninitialised).
+void bsr_alloc(Bsr& m, int n_brows, int n_bcols, int d, int dt, const std::vector<int>& rp,
+               const std::vector<int>& ci);
+// Same pattern, other dtype; values converted on the device.
+void bsr_convert(Bsr& dst, const Bsr& src, int dt, cudaStream_t s);
+// FP64 copy (same pattern) of a matrix stored in any precision.
+void bsr_widen(Bsr& dst, const Bsr& src, cudaStream_t s);
+// Explicit block transpose (pattern by counting sort on the host, values on the device).
+void bsr_transpose(Bsr& dst, const Bsr& src, cudaStream_t s);
+// Host copy of FP64 values (unpadded, nnzb*d*d).
+std::vector<double> bsr_values_host(const Bsr& m, cudaStream_t s);
+
+// Symbolic product pattern of X (nx rows) times Y: sorted unique columns per row.
+void pattern_product(const std::vector<int>& xrp, const std::vector<int>& xci, const std::vector<int>& yrp,
+                     const std::vector<int>& yci, int n_rows, std::vector<int>& crp, std::vector<int>& cci);
+// Numeric C = X Y on C's (given) pattern, FP64.
+void spgemm_numeric(Bsr& C, const Bsr& X, const Bsr& Y, cudaStream_t s);
+// C = X Y with pattern computed here (FP64).
+void spgemm(Bsr& C, const Bsr& X, const Bsr& Y, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- hierarchy
+
+struct Level {
+  int m = 0, n = 0, d = 0;
+  Bsr A;                // FP64 operator
+  Bsr As;               // smoothing copy (F32) when smooth_dt == F32
+  Bsr P, PT;            // FP64 prolongation from level+1 and its transpose
+  Bsr Ps, PTs;          // smoothing copies
+  Bsr G, GT;            // FSAI factor (non-nested) in g_dt
+  Bsr G64;              // FP64 G (kept for export)
+  Bsr F0, F0T;          // nested: outer F (in g_dt) and its transpose
+  Bsr F064, G164, A1;   // nested FP64 products kept for export
+  Bsr G1, G1T;          // nested: inner G
+  double beta = 0.0;
+  double logdet_S = 0.0;
+  // work vectors in the smoothing precision
+  void *x = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *t = nullptr, *u = nullptr;
+};
+
+struct Coarse {
+  int N = 0;
+  double* L = nullptr;  // dense lower Cholesky factor, row-major N x N
+};
+
+}  // namespace pum
+
+struct pum_hier {
+  std::vector<pum::Level> lv;
+  pum::Coarse coarse;
+  bool setup_done = false;
+  bfsai_params fp{};
+  smoother_params sp{};
+  int smooth_dt = PUM_F64;
+  int g_dt = PUM_F64;
+  std::vector<double> mu;  // Chebyshev mu_i, i = 1..k
+  // FP64 work vectors of the finest level (PCG, conversions)
+  double* w64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+struct pum_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string last_error;
+  pum::DevStatus* status = nullptr;  // device
+  double* scal = nullptr;            // device scalars (PCG)
+  double* partials = nullptr;        // device reduction partials
+  double* h_scal = nullptr;          // pinned host mirror of scal
+  int64_t launches = 0;
+  int sm_count = 152;
+  bool timing = false;
+  cudaEvent_t ev_pool[2][PUM_TK_COUNT];
+  std::vector<cudaEvent_t> tk_start[PUM_TK_COUNT], tk_stop[PUM_TK_COUNT];
+  int64_t tk_launches[PUM_TK_COUNT] = {0, 0, 0, 0};
+  double tk_ms[PUM_TK_COUNT] = {0, 0, 0, 0};
+};
+
+namespace pum {
+
+constexpr int kMaxPartials = 1 << 16;
+constexpr int kScalSlots = 32;
+
+// ----------------------------------------------------------------------------- kernels
+
+// Epilogues of the block-row product acc = (M x)_row.
+enum Epi { EPI_SET = 0, EPI_RESID = 1, EPI_ADD = 2, EPI_CHEB_FIRST0 = 3, EPI_CHEB_FIRST = 4, EPI_CHEB = 5,
+           EPI_DOT = 6 };
+
+struct EpiArgs {
+  void* y;         // output (SET/RESID/ADD/DOT) or p (CHEB*)
+  const void* b;   // RESID: right-hand side
+  void* xo;        // CHEB*: iterate updated in place
+  double mu2;      // CHEB: p <- mu2 p + acc
+  double dmu;      // CHEB*: x <- x + dmu p
+  double* partials;  // DOT: per-CTA partial sums of acc * x
+};
+
+// y (by epilogue) = M x for a BSR matrix; vector dtype vdt (F64 or F32).
+void bsr_mv(pum_ctx* ctx, const Bsr& M, int vdt, const void* x, int epi, const EpiArgs& e, int tk = -1);
+void convert_vec(pum_ctx* ctx, void* dst, int ddt, const void* src, int sdt, int64_t n);
+void zero_vec(pum_ctx* ctx, void* dst, int dt, int64_t n);
+
+// Deterministic dot product: partials then single-CTA reduction into scal[slot].
+void dot(pum_ctx* ctx, const double* a, const double* b, int64_t n, int slot);
+void dot_to(pum_ctx* ctx, const double* a, const double* b, int64_t n, double* out);
+void reduce_partials(pum_ctx* ctx, int n_partials, int slot);
+
+// Assembly, transfers (assemble.cu)
+void assemble_finest(pum_ctx* ctx, const pum_problem& pr, Level& L, double* b_dev);
+void build_prolongation(pum_ctx* ctx, int m_f, int p, int q, Level& fine);
+
+// FSAI set-up (fsai.cu)
+void fsai_setup_level(pum_ctx* ctx, pum_hier* h, int l);
+void lanczos_level(pum_ctx* ctx, pum_hier* h, int l);
+void coarse_factor(pum_ctx* ctx, pum_hier* h);
+
+// Smoother / cycle (solve.cu)
+void apply_M(pum_ctx* ctx, pum_hier* h, int l, const void* r, void* z, int tk_first);
+void cheb4(pum_ctx* ctx, pum_hier* h, int l, bool x_zero);
+void vcycle_level(pum_ctx* ctx, pum_hier* h, int l);
+void coarse_solve(pum_ctx* ctx, pum_hier* h, const void* b, void* x, int vdt);
+
+inline void count_launch(pum_ctx* ctx) { ctx->launches++; }
+void timing_begin(pum_ctx* ctx, int tk);
+void timing_end(pum_ctx* ctx, int tk);
+
+}  // namespace pum

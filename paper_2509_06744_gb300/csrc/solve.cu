@@ -1,0 +1,266 @@
+// Hot path: fourth-kind Chebyshev smoothing (Algorithm 3) with the block-FSAI
+// preconditioner M = G^T G (nested: F0^T G1^T G1 F0), the V(k,k) cycle with L2
+// transfers and a dense coarsest solve (Section 5), and the outer FP64 PCG.
+#include <cmath>
+
+#include "pum_internal.cuh"
+
+namespace pum {
+
+// ----------------------------------------------------------------------------- timing
+
+void timing_begin(pum_ctx* ctx, int tk) {
+  if (!ctx->timing) return;
+  const size_t i = (size_t)ctx->tk_launches[tk];
+  if (i >= ctx->tk_start[tk].size()) {
+    cudaEvent_t a, b;
+    PUM_CUDA(cudaEventCreate(&a));
+    PUM_CUDA(cudaEventCreate(&b));
+    ctx->tk_start[tk].push_back(a);
+    ctx->tk_stop[tk].push_back(b);
+  }
+  PUM_CUDA(cudaEventRecord(ctx->tk_start[tk][i], ctx->stream));
+}
+
+void timing_end(pum_ctx* ctx, int tk) {
+  if (!ctx->timing) return;
+  const size_t i = (size_t)ctx->tk_launches[tk];
+  PUM_CUDA(cudaEventRecord(ctx->tk_stop[tk][i], ctx->stream));
+  ctx->tk_launches[tk]++;
+}
+
+// ----------------------------------------------------------------------------- smoother
+
+static const Bsr& smoothA(pum_hier* h, int l) { return h->smooth_dt == PUM_F64 ? h->lv[l].A : h->lv[l].As; }
+
+// z = M r with the level's block-FSAI factors; the last product carries the epilogue.
+static void fsai_apply_epi(pum_ctx* ctx, pum_hier* h, int l, const void* r, int epi, EpiArgs e) {
+  Level& L = h->lv[l];
+  const int vdt = h->smooth_dt;
+  const bool fin = (l == 0);
+  EpiArgs s{};
+  if (!h->fp.nested) {
+    s.y = L.t;
+    bsr_mv(ctx, L.G, vdt, r, EPI_SET, s, fin ? PUM_TK_G : -1);
+    bsr_mv(ctx, L.GT, vdt, L.t, epi, e, fin ? PUM_TK_GT : -1);
+    return;
+  }
+  s.y = L.t;
+  bsr_mv(ctx, L.F0, vdt, r, EPI_SET, s, fin ? PUM_TK_G : -1);
+  s.y = L.u;
+  bsr_mv(ctx, L.G1, vdt, L.t, EPI_SET, s, fin ? PUM_TK_G : -1);
+  s.y = L.t;
+  bsr_mv(ctx, L.G1T, vdt, L.u, EPI_SET, s, fin ? PUM_TK_GT : -1);
+  bsr_mv(ctx, L.F0T, vdt, L.t, epi, e, fin ? PUM_TK_GT : -1);
+}
+
+void apply_M(pum_ctx* ctx, pum_hier* h, int l, const void* r, void* z, int) {
+  EpiArgs e{};
+  e.y = z;
+  fsai_apply_epi(ctx, h, l, r, EPI_SET, e);
+}
+
+// Algorithm 3 on level l with right-hand side L.b and iterate L.x (in place).
+void cheb4(pum_ctx* ctx, pum_hier* h, int l, bool x_zero) {
+  Level& L = h->lv[l];
+  const int vdt = h->smooth_dt;
+  const int k = h->sp.degree_k;
+  const double dd = 4.0 / L.beta;  // d = 4 / beta
+  const bool fin = (l == 0);
+  for (int i = 1; i <= k; ++i) {
+    const void* src = L.b;  // r = b when x0 = 0 on the first step
+    if (!(i == 1 && x_zero)) {
+      EpiArgs e{};
+      e.y = L.r;
+      e.b = L.b;
+      bsr_mv(ctx, smoothA(h, l), vdt, L.x, EPI_RESID, e, fin ? PUM_TK_RESID : -1);  // r = b - A x
+      src = L.r;
+    }
+    EpiArgs e{};
+    e.y = L.p;
+    e.xo = L.x;
+    e.dmu = dd * h->mu[i - 1];
+    int epi;
+    if (i == 1) {
+      epi = x_zero ? EPI_CHEB_FIRST0 : EPI_CHEB_FIRST;  // p = M r; x = x0 + d mu p
+    } else {
+      epi = EPI_CHEB;  // p = mu^2 p + M r; mu <- 1/(2 - mu); x = x + d mu p
+      e.mu2 = h->mu[i - 2] * h->mu[i - 2];
+    }
+    fsai_apply_epi(ctx, h, l, src, epi, e);
+  }
+}
+
+// ----------------------------------------------------------------------------- coarse solve
+
+template <typename VT>
+__global__ void k_coarse_solve(const double* __restrict__ L, int N, const VT* __restrict__ b, VT* __restrict__ x) {
+  extern __shared__ double y[];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) y[i] = (double)b[i];
+  __syncthreads();
+  for (int i = 0; i < N; ++i) {  // L y = b
+    if (threadIdx.x == 0) y[i] /= L[(int64_t)i * N + i];
+    __syncthreads();
+    const double yi = y[i];
+    for (int j = i + 1 + threadIdx.x; j < N; j += blockDim.x) y[j] -= L[(int64_t)j * N + i] * yi;
+    __syncthreads();
+  }
+  for (int i = N - 1; i >= 0; --i) {  // L^T x = y
+    if (threadIdx.x == 0) y[i] /= L[(int64_t)i * N + i];
+    __syncthreads();
+    const double xi = y[i];
+    for (int j = threadIdx.x; j < i; j += blockDim.x) y[j] -= L[(int64_t)i * N + j] * xi;
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = (VT)y[i];
+}
+
+void coarse_solve(pum_ctx* ctx, pum_hier* h, const void* b, void* x, int vdt) {
+  const int N = h->coarse.N;
+  const size_t smem = sizeof(double) * N;
+  if (vdt == PUM_F64)
+    k_coarse_solve<double><<<1, 256, smem, ctx->stream>>>(h->coarse.L, N, (const double*)b, (double*)x);
+  else
+    k_coarse_solve<float><<<1, 256, smem, ctx->stream>>>(h->coarse.L, N, (const float*)b, (float*)x);
+  count_launch(ctx);
+  PUM_CUDA(cudaGetLastError());
+}
+
+// ----------------------------------------------------------------------------- V-cycle
+
+void vcycle_level(pum_ctx* ctx, pum_hier* h, int l) {
+  Level& L = h->lv[l];
+  const int vdt = h->smooth_dt;
+  if (l == (int)h->lv.size() - 1) {
+    coarse_solve(ctx, h, L.b, L.x, vdt);
+    return;
+  }
+  Level& C = h->lv[l + 1];
+  const Bsr& PT = vdt == PUM_F64 ? L.PT : L.PTs;
+  const Bsr& P = vdt == PUM_F64 ? L.P : L.Ps;
+  cheb4(ctx, h, l, true);  // pre-smoothing from x0 = 0
+  EpiArgs e{};
+  e.y = L.r;
+  e.b = L.b;
+  bsr_mv(ctx, smoothA(h, l), vdt, L.x, EPI_RESID, e, l == 0 ? PUM_TK_RESID : -1);  // r = b - A x
+  EpiArgs rs{};
+  rs.y = C.b;
+  bsr_mv(ctx, PT, vdt, L.r, EPI_SET, rs);  // b_c = P^T r
+  vcycle_level(ctx, h, l + 1);
+  EpiArgs pa{};
+  pa.y = L.x;
+  bsr_mv(ctx, P, vdt, C.x, EPI_ADD, pa);  // x += P x_c
+  cheb4(ctx, h, l, false);  // post-smoothing, same polynomial
+}
+
+// ----------------------------------------------------------------------------- PCG
+
+enum { S_RZ = 0, S_PQ = 1, S_RR = 2, S_RZN = 3, S_RZO = 4, S_BB = 5 };
+
+// x += alpha p, r -= alpha q with alpha = scal[RZ] / scal[PQ]; partial sums of r.r
+__global__ void k_pcg_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                         const double* __restrict__ q, const double* __restrict__ scal, int64_t n,
+                         double* __restrict__ partials) {
+  __shared__ double red[8];
+  const double alpha = scal[S_RZ] / scal[S_PQ];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const double ri = fma(-alpha, q[i], r[i]);
+    r[i] = ri;
+    s = fma(ri, ri, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    partials[blockIdx.x] = t;
+  }
+}
+
+// p = z + beta p, beta = (scal[RZN] - flex * scal[RZO]) / scal[RZ]
+__global__ void k_pcg_p(double* __restrict__ p, const double* __restrict__ z, const double* __restrict__ scal,
+                        int flexible, int64_t n) {
+  const double beta = (scal[S_RZN] - (flexible ? scal[S_RZO] : 0.0)) / scal[S_RZ];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], z[i]);
+}
+
+__global__ void k_scal_move(double* scal, int dst, int src) { scal[dst] = scal[src]; }
+
+static void vcycle64(pum_ctx* ctx, pum_hier* h, const double* r, double* z) {
+  Level& L0 = h->lv[0];
+  const int64_t N = (int64_t)L0.n * L0.d;
+  convert_vec(ctx, L0.b, h->smooth_dt, r, PUM_F64, N);
+  vcycle_level(ctx, h, 0);
+  convert_vec(ctx, z, PUM_F64, L0.x, h->smooth_dt, N);
+}
+
+void vcycle_apply_impl(pum_ctx* ctx, pum_hier* h, const double* r, double* z) { vcycle64(ctx, h, r, z); }
+
+pum_status pcg_impl(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_report* rep) {
+  Level& L0 = h->lv[0];
+  const int64_t N = (int64_t)L0.n * L0.d;
+  cudaStream_t s = ctx->stream;
+  double *r = h->w64[0], *z = h->w64[1], *p = h->w64[2], *q = h->w64[3], *zo = h->w64[4];
+  const int grid = (int)std::min<int64_t>((N + 255) / 256, 1024);
+  const unsigned mvgrid = (unsigned)((N + 255) / 256);
+  PUM_CHECK(mvgrid <= (1u << 16), PUM_ERR_UNSUPPORTED, "PCG: problem too large for the partial buffer");
+  PUM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * N, s));
+  PUM_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  dot(ctx, b, b, N, S_BB);
+  PUM_CUDA(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+  PUM_CUDA(cudaStreamSynchronize(s));
+  const double nb = std::sqrt(ctx->h_scal[S_BB]);
+  rep->iters = 0;
+  rep->converged = 0;
+  rep->final_relres = 1.0;
+  if (rep->hist && rep->maxit >= 0) rep->hist[0] = 1.0;
+  if (nb == 0.0) {
+    rep->converged = 1;
+    rep->final_relres = 0.0;
+    return PUM_OK;
+  }
+  vcycle64(ctx, h, r, z);
+  dot(ctx, r, z, N, S_RZ);
+  PUM_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  for (int it = 1; it <= rep->maxit; ++it) {
+    EpiArgs e{};
+    e.y = q;
+    e.partials = ctx->partials;
+    bsr_mv(ctx, L0.A, PUM_F64, p, EPI_DOT, e, PUM_TK_PCG_AP);  // q = A p, partials of p.q
+    reduce_partials(ctx, (int)mvgrid, S_PQ);
+    k_pcg_xr<<<grid, 256, 0, s>>>(x, r, p, q, ctx->scal, N, ctx->partials);
+    count_launch(ctx);
+    reduce_partials(ctx, grid, S_RR);
+    PUM_CUDA(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+    PUM_CUDA(cudaStreamSynchronize(s));
+    const double pq = ctx->h_scal[S_PQ], rr = ctx->h_scal[S_RR], rz = ctx->h_scal[S_RZ];
+    if (!(pq > 0.0) || !std::isfinite(rr) || !std::isfinite(rz)) {
+      rep->iters = it;
+      throw Error{PUM_ERR_BREAKDOWN, "PCG breakdown: p^T A p = " + std::to_string(pq) + ", r^T z = " +
+                                         std::to_string(rz)};
+    }
+    const double rel = std::sqrt(rr) / nb;
+    if (rep->hist) rep->hist[it] = rel;
+    rep->iters = it;
+    rep->final_relres = rel;
+    if (rel <= rep->rtol) {
+      rep->converged = 1;
+      return PUM_OK;
+    }
+    if (rep->flexible) PUM_CUDA(cudaMemcpyAsync(zo, z, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    vcycle64(ctx, h, r, z);
+    dot(ctx, r, z, N, S_RZN);
+    if (rep->flexible) dot(ctx, r, zo, N, S_RZO);
+    k_pcg_p<<<grid, 256, 0, s>>>(p, z, ctx->scal, rep->flexible, N);
+    k_scal_move<<<1, 1, 0, s>>>(ctx->scal, S_RZ, S_RZN);
+    ctx->launches += 2;
+    PUM_CUDA(cudaGetLastError());
+  }
+  return PUM_ERR_NOCONV;
+}
+
+}  // namespace pum

@@ -78,6 +78,11 @@ class Problem:
     g_dtype: str             # "f64", "f32", "bf16"
 
     @property
+    def nitsche(self) -> tuple:
+        """Constants C_j of the Nitsche penalties gamma^(j) = C_j (p+1)^2 h^-(order-1-2j)."""
+        return NITSCHE_CONSTANTS[self.equation]
+
+    @property
     def d(self) -> int:
         return (self.p + 1) * (self.p + 2) // 2
 
@@ -85,6 +90,10 @@ class Problem:
     def n_dofs(self) -> int:
         return self.d * self.finest_m ** 2
 
+
+# Nitsche penalty constants per equation order: the smallest round values for which the
+# assembled stiffness matrices are SPD on 2..16 patches per side.
+NITSCHE_CONSTANTS = {4: (4.0, 2.0, 0.0), 6: (1.0e4, 1.0e2, 1.0)}
 
 # The workloads of the benchmark suite, with their sizes.
 SMALL_BIHARMONIC = Problem("biharmonic p=3 16x16 patches, 4 levels, static block-FSAI, Chebyshev-4 k=2",

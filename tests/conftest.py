@@ -20,4 +20,4 @@ def small_biharmonic():
     import pum_inputs as pin
     pr = pin.SMALL_BIHARMONIC
     f = pum.fourier_source(pin.fourier_coefficients(pr.rhs_seed), pr.rhs_decay)
-    return pum.build_hierarchy(pr.finest_m, pr.p, pr.equation, pr.n_levels, f=f)
+    return pum.build_hierarchy(pr.finest_m, pr.p, pr.equation, pr.n_levels, f=f, constants=pr.nitsche)

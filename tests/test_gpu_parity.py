@@ -1,0 +1,340 @@
+"""GPU parity: every step of the CUDA path against the FP64 oracle on the same seeded inputs.
+
+Sizes: the 16x16-patch biharmonic p=3 problem (4 levels, 2,560 unknowns), an 8x8
+triharmonic p=5 problem, a 6x6 p=2 problem (non-power-of-two, ragged thread tails)
+and small random block matrices for block sizes 3, 6, 10, 15 and 21.
+"""
+import numpy as np
+import pytest
+
+import pum_inputs as pin
+from oracle import blocks as bk
+from oracle import cheb, fsai, pum, solver
+from _util import (TOL_ASSEMBLY, TOL_FSAI, TOL_HISTORY, TOL_VECTOR, assert_same_pattern, cuda, from_export, host,
+                   max_rel, norm_rel, to_pview, to_view)
+
+pytestmark = pytest.mark.gpu
+
+PR = pin.SMALL_BIHARMONIC
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2509_06744_gb300 as L
+    return L
+
+
+@pytest.fixture(scope="module")
+def ctx(lib):
+    c = lib.Context(0)
+    yield c
+    c.close()
+
+
+def hier_from_oracle(lib, ctx, h):
+    return lib.Hierarchy.from_bsr(ctx, [to_view(A) for A in h.A], [to_pview(P) for P in h.P])
+
+
+# --------------------------------------------------------------------------- assembly
+
+def test_assembly_and_galerkin_hierarchy_match_oracle(lib, ctx, small_biharmonic):
+    h = small_biharmonic
+    import torch
+    b = torch.zeros(PR.n_dofs, dtype=torch.float64, device="cuda")
+    H = lib.Hierarchy.assemble(ctx, PR.equation, PR.p, PR.finest_m, PR.n_levels,
+                               f_coef=pin.fourier_coefficients(PR.rhs_seed), f_decay=PR.rhs_decay,
+                               nitsche=PR.nitsche, b=b)
+    assert max_rel(host(b), h.b) <= TOL_ASSEMBLY
+    for l in range(PR.n_levels):
+        A = from_export(H.export(l, lib.PUM_MAT_A))
+        assert_same_pattern(A, h.A[l])
+        assert max_rel(A.blocks, h.A[l].blocks) <= TOL_ASSEMBLY, f"level {l}"
+    for l in range(PR.n_levels - 1):
+        P = from_export(H.export(l, lib.PUM_MAT_P))
+        assert_same_pattern(P, h.P[l])
+        assert max_rel(P.blocks, h.P[l].blocks) <= TOL_ASSEMBLY
+
+
+@pytest.mark.parametrize("order,p,m,levels", [(6, 5, 8, 2), (4, 2, 6, 2), (4, 1, 4, 3), (6, 4, 4, 2)])
+def test_assembly_other_equations_and_degrees(lib, ctx, order, p, m, levels):
+    """Triharmonic p=5, p=1/2/4 block sizes, and a non-power-of-two cover."""
+    import torch
+    coef = pin.fourier_coefficients(7)
+    consts = pin.NITSCHE_CONSTANTS[order]
+    f = pum.fourier_source(coef, 3.0)
+    ref = pum.build_hierarchy(m, p, order, levels, f=f, constants=consts)
+    b = torch.zeros(m * m * pum.local_dim(p), dtype=torch.float64, device="cuda")
+    H = lib.Hierarchy.assemble(ctx, order, p, m, levels, f_coef=coef, f_decay=3.0, nitsche=consts, b=b)
+    assert max_rel(host(b), ref.b) <= TOL_ASSEMBLY
+    for l in range(levels):
+        A = from_export(H.export(l, lib.PUM_MAT_A))
+        assert_same_pattern(A, ref.A[l])
+        assert max_rel(A.blocks, ref.A[l].blocks) <= TOL_ASSEMBLY
+    for l in range(levels - 1):
+        P = from_export(H.export(l, lib.PUM_MAT_P))
+        assert_same_pattern(P, ref.P[l])
+        assert max_rel(P.blocks, ref.P[l].blocks) <= TOL_ASSEMBLY
+
+
+# --------------------------------------------------------------------------- FSAI
+
+@pytest.fixture(scope="module")
+def static_pair(lib, ctx, small_biharmonic):
+    H = hier_from_oracle(lib, ctx, small_biharmonic)
+    H.setup(p0="lower", adaptive=False, k=PR.cheb_k)
+    ref = solver.build_setup(small_biharmonic, k=PR.cheb_k, mode="static", P0="lower")
+    return H, ref
+
+
+def test_static_fsai_pattern_bit_exact_and_values(lib, static_pair, small_biharmonic):
+    H, _ = static_pair
+    for l in range(PR.n_levels - 1):
+        A = small_biharmonic.A[l]
+        ref = fsai.fsai(A, fsai.lower_pattern(A))
+        G = from_export(H.export(l, lib.PUM_MAT_G))
+        assert_same_pattern(G, ref.G)
+        assert max_rel(G.blocks, ref.G.blocks) <= TOL_FSAI
+        # Kaporin-type measure sum log det S_kk (Lemma 2.7)
+        assert abs(H.info(l)["logdet_S"] - ref.logdet_S()) <= 1e-10 * abs(ref.logdet_S())
+
+
+def test_lanczos_beta_matches_oracle(static_pair):
+    H, ref = static_pair
+    for l in range(PR.n_levels - 1):
+        assert abs(H.info(l)["beta"] - ref.levels[l].beta) <= 1e-10 * ref.levels[l].beta
+
+
+@pytest.fixture(scope="module")
+def adaptive_ref(small_biharmonic):
+    return [fsai.adaptive_fsai(A, fsai.lower_pattern(A), 6).fsai for A in small_biharmonic.A[:-1]]
+
+
+def test_adaptive_fsai_patterns_bit_exact(lib, ctx, small_biharmonic, adaptive_ref):
+    """Algorithm 1 with P0 = lower(P(A)), t_max = 6, tau = 1: the same blocks chosen in every row."""
+    H = hier_from_oracle(lib, ctx, small_biharmonic)
+    H.setup(p0="lower", adaptive=True, t_max=6, tau=1.0, k=3)
+    for l, ref in enumerate(adaptive_ref):
+        G = from_export(H.export(l, lib.PUM_MAT_G))
+        assert_same_pattern(G, ref.G)
+        assert max_rel(G.blocks, ref.G.blocks) <= TOL_FSAI
+
+
+def test_adaptive_fsai_from_diagonal_pattern(lib, ctx, small_biharmonic):
+    """The paper's default P0 = diagonal (Section 5), t_max = 4."""
+    A = small_biharmonic.A[1]
+    ref = fsai.adaptive_fsai(A, fsai.diag_pattern(A.n_rows), 4).fsai
+    H = lib.Hierarchy.from_bsr(ctx, [to_view(A), to_view(small_biharmonic.A[2])], [to_pview(small_biharmonic.P[1])])
+    H.setup(p0="diag", adaptive=True, t_max=4, tau=1.0, k=2)
+    G = from_export(H.export(0, lib.PUM_MAT_G))
+    assert_same_pattern(G, ref.G)
+    assert max_rel(G.blocks, ref.G.blocks) <= TOL_FSAI
+
+
+def test_nested_fsai_patterns_and_factors(lib, ctx, small_biharmonic):
+    """Section 2.2: F0, A1 = F0 A F0^T and the inner G1 match (patterns bit-exact)."""
+    A = small_biharmonic.A[1]
+    ref = fsai.nested_fsai(A, fsai.diag_pattern(A.n_rows), 3)
+    H = lib.Hierarchy.from_bsr(ctx, [to_view(A), to_view(small_biharmonic.A[2])], [to_pview(small_biharmonic.P[1])])
+    H.setup(p0="diag", adaptive=True, t_max=3, tau=1.0, nested=True, k=2)
+    F0 = from_export(H.export(0, lib.PUM_MAT_F0))
+    A1 = from_export(H.export(0, lib.PUM_MAT_A1))
+    G1 = from_export(H.export(0, lib.PUM_MAT_G1))
+    assert_same_pattern(F0, ref.F0)
+    assert_same_pattern(A1, ref.A1)
+    assert_same_pattern(G1, ref.inner.G)
+    assert max_rel(F0.blocks, ref.F0.blocks) <= TOL_FSAI
+    assert max_rel(A1.blocks, ref.A1.blocks) <= TOL_FSAI
+    assert max_rel(G1.blocks, ref.inner.G.blocks) <= 1e3 * TOL_FSAI
+    # the smoother applies F0^T G1^T G1 F0
+    r = pin.normal_vector(A.n_rows * A.d, 3)
+    z = cuda(np.zeros_like(r))
+    H.fsai_apply(0, cuda(r), z)
+    assert norm_rel(host(z), ref.apply(r)) <= 1e3 * TOL_VECTOR
+
+
+# --------------------------------------------------------------------------- single steps
+
+def test_single_steps_match_oracle(lib, ctx, static_pair, small_biharmonic):
+    H, ref = static_pair
+    h = small_biharmonic
+    for l in range(PR.n_levels - 1):
+        A, P = h.A[l], h.P[l]
+        N, Nc = A.n_rows * A.d, P.n_cols * P.d
+        x, b = pin.normal_vector(N, 10 + l), pin.normal_vector(N, 20 + l)
+        r = cuda(np.zeros(N))
+        H.residual(l, cuda(b), cuda(x), r)
+        assert norm_rel(host(r), b - A.matvec(x)) <= 1e-13
+        z = cuda(np.zeros(N))
+        H.fsai_apply(l, cuda(b), z)
+        assert norm_rel(host(z), ref.levels[l].M(b)) <= TOL_VECTOR
+        rc = cuda(np.zeros(Nc))
+        H.restrict(l, cuda(b), rc)
+        assert norm_rel(host(rc), P.to_scipy().T @ b) <= 1e-13
+        ec = pin.normal_vector(Nc, 30 + l)
+        xx = cuda(x)
+        H.prolong_add(l, cuda(ec), xx)
+        assert norm_rel(host(xx), x + P.matvec(ec)) <= 1e-13
+    Ac = h.A[-1].to_dense()
+    rc = pin.normal_vector(Ac.shape[0], 40)
+    zc = cuda(np.zeros_like(rc))
+    H.coarse_solve(cuda(rc), zc)
+    assert norm_rel(host(zc), np.linalg.solve(Ac, rc)) <= 1e-11
+
+
+@pytest.mark.parametrize("x_zero", [True, False])
+def test_chebyshev_smoother_matches_algorithm3(lib, static_pair, small_biharmonic, x_zero):
+    H, ref = static_pair
+    for l in range(PR.n_levels - 1):
+        A = small_biharmonic.A[l]
+        N = A.n_rows * A.d
+        b = pin.normal_vector(N, 50 + l)
+        x0 = np.zeros(N) if x_zero else pin.normal_vector(N, 60 + l)
+        xg = cuda(x0)
+        H.cheb4_smooth(l, cuda(b), xg, x_zero)
+        lev = ref.levels[l]
+        xr = cheb.cheb4(A.matvec, lev.M, b, None if x_zero else x0, lev.beta, PR.cheb_k)
+        assert norm_rel(host(xg), xr) <= TOL_VECTOR
+
+
+def test_vcycle_matches_oracle_and_is_deterministic(lib, static_pair, small_biharmonic):
+    H, ref = static_pair
+    r = pin.normal_vector(PR.n_dofs, 70)
+    z1, z2 = cuda(np.zeros_like(r)), cuda(np.zeros_like(r))
+    H.vcycle(cuda(r), z1)
+    H.vcycle(cuda(r), z2)
+    assert np.array_equal(host(z1), host(z2)), "V-cycle is not bitwise reproducible"
+    assert norm_rel(host(z1), solver.vcycle(ref, r)) <= TOL_VECTOR
+
+
+def test_pcg_histories_match_oracle(lib, static_pair, small_biharmonic):
+    """FP64 path: same iteration count and ||r_j||/||b|| histories within 1e-12."""
+    H, ref = static_pair
+    h = small_biharmonic
+    x = cuda(np.zeros_like(h.b))
+    rep = H.pcg(cuda(h.b), x, rtol=1e-8, maxit=100)
+    res = solver.solve(ref, h.b, rtol=1e-8)
+    assert rep["converged"] and rep["iters"] == res.iters
+    assert np.max(np.abs(np.array(rep["history"]) - np.array(res.history))) <= TOL_HISTORY
+    assert norm_rel(host(x), res.x) <= 1e-9
+
+
+def test_end_to_end_gpu_assembly_and_setup(lib, ctx, small_biharmonic):
+    """GPU assembly + GPU static FSAI + PCG against the oracle's whole pipeline."""
+    import torch
+    h = small_biharmonic
+    b = torch.zeros(PR.n_dofs, dtype=torch.float64, device="cuda")
+    H = lib.Hierarchy.assemble(ctx, PR.equation, PR.p, PR.finest_m, PR.n_levels,
+                               f_coef=pin.fourier_coefficients(PR.rhs_seed), f_decay=PR.rhs_decay,
+                               nitsche=PR.nitsche, b=b)
+    H.setup(p0="lower", adaptive=False, k=PR.cheb_k)
+    ref = solver.build_setup(h, k=PR.cheb_k, mode="static", P0="lower")
+    res = solver.solve(ref, h.b, rtol=1e-8)
+    x = torch.zeros_like(b)
+    rep = H.pcg(b, x, rtol=1e-8, maxit=100)
+    assert rep["iters"] == res.iters
+    assert np.max(np.abs(np.array(rep["history"]) - np.array(res.history))) <= TOL_HISTORY
+
+
+@pytest.mark.parametrize("g", ["f32", "bf16"])
+def test_fp32_smoothing_fp64_outer_reaches_tolerance(lib, ctx, small_biharmonic, g):
+    """FP32 smoother (A, P, vectors) with G in FP32 or BF16 under flexible FP64 PCG."""
+    h = small_biharmonic
+    H = hier_from_oracle(lib, ctx, h)
+    H.setup(p0="lower", adaptive=False, k=PR.cheb_k, smooth="f32", g=g)
+    x = cuda(np.zeros_like(h.b))
+    rep = H.pcg(cuda(h.b), x, rtol=1e-8, maxit=100, flexible=True)
+    assert rep["converged"]
+    A = h.A[0]
+    xs = host(x)
+    true_rel = np.linalg.norm(h.b - A.matvec(xs)) / np.linalg.norm(h.b)
+    assert true_rel <= 5e-8
+    ref = solver.solve(solver.build_setup(h, k=PR.cheb_k, mode="static", P0="lower"), h.b, rtol=1e-10)
+    assert norm_rel(xs, ref.x) <= 1e-5
+
+
+def test_save_load_roundtrip_bitwise(lib, ctx, static_pair, tmp_path):
+    H, _ = static_pair
+    path = str(tmp_path / "hier.bin")
+    H.save(path)
+    H2 = lib.Hierarchy.load(ctx, path)
+    r = pin.normal_vector(PR.n_dofs, 80)
+    z1, z2 = cuda(np.zeros_like(r)), cuda(np.zeros_like(r))
+    H.vcycle(cuda(r), z1)
+    H2.vcycle(cuda(r), z2)
+    assert np.array_equal(host(z1), host(z2))
+    for l in range(PR.n_levels):
+        assert H2.info(l)["beta"] == H.info(l)["beta"]
+
+
+# --------------------------------------------------------------------------- block sizes, edges
+
+def _random_block_spd(n_side, d, seed):
+    """SPD block matrix with the 3x3 stencil of an n_side x n_side cover."""
+    rng = np.random.default_rng(seed)
+    n = n_side * n_side
+    ent = {}
+    for i in range(n):
+        ix, iy = i % n_side, i // n_side
+        for jy in range(max(iy - 1, 0), min(iy + 2, n_side)):
+            for jx in range(max(ix - 1, 0), min(ix + 2, n_side)):
+                j = jy * n_side + jx
+                if j < i:
+                    blk = 0.1 * rng.standard_normal((d, d))
+                    ent[(i, j)] = blk
+                    ent[(j, i)] = blk.T
+        Q = rng.standard_normal((d, d))
+        ent[(i, i)] = Q @ Q.T + 10.0 * d * np.eye(d)
+    return bk.from_blocks(n, n, d, ent)
+
+
+@pytest.mark.parametrize("d", [3, 6, 10, 15, 21])
+def test_block_sizes_residual_and_static_fsai(lib, ctx, d):
+    """Every supported block size, with a row count that leaves a ragged last thread block."""
+    A = _random_block_spd(5, d, seed=d)
+    H = lib.Hierarchy.from_bsr(ctx, [to_view(A)], [])
+    N = A.n_rows * d
+    x, b = pin.normal_vector(N, 1), pin.normal_vector(N, 2)
+    r = cuda(np.zeros(N))
+    H.residual(0, cuda(b), cuda(x), r)
+    assert norm_rel(host(r), b - A.matvec(x)) <= 1e-13
+    # one-level hierarchy: the cycle is the coarse solve
+    H.setup(p0="lower", k=1)
+    z = cuda(np.zeros(N))
+    H.vcycle(cuda(b), z)
+    assert norm_rel(host(z), np.linalg.solve(A.to_dense(), b)) <= 1e-11
+    # two-level hierarchy to exercise the FSAI rows at this block size
+    P = bk.from_blocks(A.n_rows, 1, d, {(i, 0): np.eye(d) for i in range(A.n_rows)})
+    H2 = lib.Hierarchy.from_bsr(ctx, [to_view(A), None], [to_pview(P)])
+    H2.setup(p0="lower", k=2)
+    ref = fsai.fsai(A, fsai.lower_pattern(A))
+    G = from_export(H2.export(0, lib.PUM_MAT_G))
+    assert_same_pattern(G, ref.G)
+    assert max_rel(G.blocks, ref.G.blocks) <= TOL_FSAI
+
+
+def test_invalid_arguments_are_reported(lib, ctx, static_pair):
+    import torch
+    H, _ = static_pair
+    good = torch.zeros(PR.n_dofs + 2, dtype=torch.float64, device="cuda")
+    misaligned = good[1:PR.n_dofs + 1]
+    with pytest.raises(lib.PumError) as e:
+        H.vcycle(misaligned, good[:PR.n_dofs])
+    assert e.value.status == 1
+    with pytest.raises(lib.PumError):
+        H.residual(7, good[:PR.n_dofs], good[:PR.n_dofs], good[:PR.n_dofs])
+    bad = bk.from_blocks(2, 2, 4, {(0, 0): np.eye(4), (1, 1): np.eye(4)})
+    with pytest.raises(lib.PumError) as e:
+        lib.Hierarchy.from_bsr(ctx, [to_view(bad)], [])
+    assert e.value.status == 8  # block size 4 is not a PUM block size
+
+
+def test_indefinite_matrix_reports_not_spd(lib, ctx):
+    """A non-SPD operator is reported by the device status word, not by a fault."""
+    A = _random_block_spd(3, 6, seed=1)
+    A.blocks[A.indptr[4] + list(A.row(4)).index(4)] *= -1.0
+    P = bk.from_blocks(A.n_rows, 1, 6, {(i, 0): np.eye(6) for i in range(A.n_rows)})
+    H = lib.Hierarchy.from_bsr(ctx, [to_view(A), None], [to_pview(P)])
+    with pytest.raises(lib.PumError) as e:
+        H.setup(p0="lower", k=2)
+    assert e.value.status == 4
+    ctx.sync()  # the context stays usable

@@ -1,0 +1,62 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point of include/pum.h.
+
+No GPU is needed: only calls that fail before touching a device are made here.
+"""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "pum.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\**\s+\**([a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2509_06744_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ["pum_assemble", "bfsai_setup", "cheb4_smooth", "vcycle_apply", "pcg_solve",
+                     "pum_hier_from_bsr", "pum_create", "pum_destroy", "pum_hier_save", "pum_hier_load"]:
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_library_built_for_sm103a():
+    from paper_2509_06744_gb300 import build
+    assert "arch=compute_103a,code=sm_103a" in build.ARCH
+
+
+def test_null_arguments_are_rejected_without_a_device(lib):
+    from paper_2509_06744_gb300 import _lib
+    assert lib.pum_create(None, 0, None) == _lib.PUM_ERR_INVALID_ARG
+    assert lib.pum_destroy(None) == _lib.PUM_ERR_INVALID_ARG
+    assert lib.pum_hier_destroy(None) == _lib.PUM_ERR_INVALID_ARG
+    assert lib.pum_last_error(None) == b"NULL context"
+    assert lib.pum_launch_count(None) == 0
+    n = C.c_int32()
+    assert lib.pum_hier_levels(None, C.byref(n)) == _lib.PUM_ERR_INVALID_ARG
+
+
+def test_missing_device_is_an_error_not_a_fallback(lib):
+    """On a machine without a CUDA device the library refuses to create a context."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    from paper_2509_06744_gb300 import Context, PumError
+    with pytest.raises(PumError):
+        Context(0)
