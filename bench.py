@@ -171,6 +171,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="FP32 form only: one solve bracketed by cudaProfilerStart/Stop (for ncu "
+                         "--profile-from-start off); prints the launch count")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -194,6 +197,24 @@ def main():
     N = pr.n_dofs
     b = torch.zeros(N, dtype=torch.float64, device="cuda")
     t_setup = time.perf_counter()
+    if args.profile:
+        H = pum.Hierarchy.assemble(ctx, pr.equation, pr.p, pr.finest_m, pr.n_levels,
+                                   f_coef=pin.fourier_coefficients(pr.rhs_seed), f_decay=pr.rhs_decay,
+                                   nitsche=pr.nitsche, b=b)
+        H.setup(p0=pr.fsai_p0, adaptive=pr.adaptive, t_max=pr.t_max, tau=pr.tau, k=pr.cheb_k, smooth="f32",
+                g="f32")
+        x = torch.zeros_like(b)
+        for _ in range(args.warmup):
+            H.pcg(b, x, rtol=RTOL, maxit=200, flexible=True)
+        torch.cuda.synchronize()
+        l0 = ctx.launches
+        torch.cuda.profiler.start()
+        rep = H.pcg(b, x, rtol=RTOL, maxit=200, flexible=True)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile": "one FP32-smoothing PCG solve", "launches": ctx.launches - l0,
+                          "iters": rep["iters"]}), flush=True)
+        return
     H = pum.Hierarchy.assemble(ctx, pr.equation, pr.p, pr.finest_m, pr.n_levels,
                                f_coef=pin.fourier_coefficients(pr.rhs_seed), f_decay=pr.rhs_decay,
                                nitsche=pr.nitsche, b=b)
