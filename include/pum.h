@@ -197,6 +197,25 @@ pum_status pum_prolong_add(pum_ctx *ctx, pum_hier *h, int level, const double *e
 /* z = A_c^{-1} r on the coarsest level (dense Cholesky). */
 pum_status pum_coarse_solve(pum_ctx *ctx, pum_hier *h, const double *r, double *z);
 
+/* ---- without allocation ------------------------------------------------------------- */
+
+/* z = G^T (G r) for a caller-held block-FSAI factor G (square, block size 3/6/10/15/21) and
+ * its explicit block transpose GT, both as DEVICE BSR arrays (on_device = 1, float64,
+ * blocks contiguous d x d row-major, columns sorted; the pattern is not re-validated).
+ * The paper has no counterpart: this exists for callers that must not allocate device
+ * memory -- inside a CUDA graph capture, in a loop that cannot afford the device-wide
+ * synchronisation of cudaMalloc/cudaFree, or when all memory is held by another
+ * allocator.  It calls no cudaMalloc/cudaFree: the intermediate G r lives in a static
+ * device array of 2^20 doubles (8 MiB) held by every GPU that loads the library until
+ * exit, so G may have at most 1,048,576 unknowns (larger: PUM_ERR_INVALID_ARG).  The
+ * first call on a device looks up that array's device address (with the device
+ * current); make that first call before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU (other streams or contexts on the same device)
+ * race; calls queued on one stream are safe.  r, z: device float64, 16-byte aligned,
+ * length n_brows*bs; queued on the context's stream. */
+pum_status pum_fsai_apply_noalloc(pum_ctx *ctx, const pum_bsr_view *G, const pum_bsr_view *GT, const double *r,
+                                  double *z);
+
 /* ---- inspection, persistence ------------------------------------------------------- */
 
 pum_status pum_hier_levels(const pum_hier *h, int *n_levels);

@@ -84,6 +84,7 @@ _SIGNATURES = {
     "pum_timing_reset": (c_int32, [c_void_p]),
     "pum_timing_read": (c_int32, [c_void_p, P(c_int64), P(c_double)]),
     "pum_launch_count": (c_int64, [c_void_p]),
+    "pum_fsai_apply_noalloc": (c_int32, [c_void_p, P(BsrView), P(BsrView), c_void_p, c_void_p]),
 }
 
 _LIB = None
