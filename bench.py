@@ -50,6 +50,7 @@ def algorithmic_bytes(info, smooth_bytes, g_bytes, vec_bytes):
         "g": info["nnzb_G"] * (d * d * g_bytes + 4) + 2 * N * vec_bytes,             # r read; t write
         "gt": info["nnzb_G"] * (d * d * g_bytes + 4) + 5 * N * vec_bytes,            # t, p, x read; p, x write
         "pcg_ap": info["nnzb_A"] * (d * d * 8 + 4) + 2 * N * 8,                        # A (FP64), p read; q write
+        "resid64": info["nnzb_A"] * (d * d * 8 + 4) + 3 * N * vec_bytes,              # FP64 A on FP32 vectors
     }
 
 
@@ -296,7 +297,7 @@ def main():
     info = H.info(0)
     ab = algorithmic_bytes(info, 4, 4, 4)
     peak, peak_kind = load_peaks()
-    classes = {k: v for k, v in kt.items() if k != "pcg_ap" and v[0] > 0}
+    classes = {k: v for k, v in kt.items() if k in ("resid", "g", "gt") and v[0] > 0}
     dom = max(classes, key=lambda k: classes[k][1])
     n_l, ms_l = classes[dom]
     avg_s = ms_l / n_l * 1e-3

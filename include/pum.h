@@ -103,6 +103,8 @@ typedef struct {
   uint64_t lanczos_seed; /* SplitMix64 seed of the start vector; level l uses seed + l     */
   int32_t smooth_dt;     /* PUM_F64 or PUM_F32: storage and arithmetic of A, P and vectors  */
   int32_t g_dt;          /* PUM_F64, PUM_F32 or PUM_BF16 (BF16 needs smooth_dt = PUM_F32)   */
+  int32_t resid_f64;     /* FP32 form: 1 forms the residual restricted to the next level with
+                            the FP64 operator and FP64 sums (vectors stay FP32)              */
 } smoother_params;
 
 /* Outer preconditioned CG (one V(k,k) cycle as preconditioner). */
@@ -233,10 +235,11 @@ pum_status pum_hier_destroy(pum_hier *h);
 
 /* Per-kernel-class timing of the hot path.  When enabled, every launch of the classes
  * below on the finest level is bracketed by CUDA events recorded on the launching
- * stream; pum_timing_read returns, per class, the number of launches and the summed
- * event time since the last reset.  Class ids: 0 residual A x (smoother), 1 G r,
- * 2 G^T t + Chebyshev update, 3 A p in PCG. */
-enum { PUM_TK_RESID = 0, PUM_TK_G = 1, PUM_TK_GT = 2, PUM_TK_PCG_AP = 3, PUM_TK_COUNT = 4 };
+ * stream (inside the captured V-cycle graph when one is used); pum_timing_read returns,
+ * per class, the number of launches and the summed event time since the last reset.
+ * Class ids: 0 residual b - A x in the smoother's precision, 1 G r, 2 G^T t + Chebyshev
+ * update, 3 A p in PCG, 4 residual with the FP64 operator on FP32 vectors. */
+enum { PUM_TK_RESID = 0, PUM_TK_G = 1, PUM_TK_GT = 2, PUM_TK_PCG_AP = 3, PUM_TK_RESID64 = 4, PUM_TK_COUNT = 5 };
 pum_status pum_timing_enable(pum_ctx *ctx, int enable);
 pum_status pum_timing_reset(pum_ctx *ctx);
 pum_status pum_timing_read(pum_ctx *ctx, int64_t *launches, double *ms);

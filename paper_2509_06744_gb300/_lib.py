@@ -15,7 +15,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_SPD", 5:
 PUM_F64, PUM_F32, PUM_BF16 = 0, 1, 2
 PUM_P0_LOWER, PUM_P0_DIAG = 0, 1
 PUM_MAT_A, PUM_MAT_P, PUM_MAT_G, PUM_MAT_GT, PUM_MAT_F0, PUM_MAT_G1, PUM_MAT_A1 = range(7)
-PUM_TK_COUNT = 4
+PUM_TK_COUNT = 5
 CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream
 
 
@@ -42,7 +42,7 @@ class FsaiParams(C.Structure):
 
 class SmootherParams(C.Structure):
     _fields_ = [("degree_k", c_int32), ("lanczos_its", c_int32), ("lanczos_safety", c_double),
-                ("lanczos_seed", C.c_uint64), ("smooth_dt", c_int32), ("g_dt", c_int32)]
+                ("lanczos_seed", C.c_uint64), ("smooth_dt", c_int32), ("g_dt", c_int32), ("resid_f64", c_int32)]
 
 
 class PcgReport(C.Structure):

@@ -3,6 +3,7 @@
 // library errors and CUDA failures and returns a pum_status.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -58,14 +59,15 @@ void free_level(Level& L) {
   for (Bsr* m : {&L.A, &L.As, &L.P, &L.PT, &L.Ps, &L.PTs, &L.G, &L.GT, &L.G64, &L.F0, &L.F0T, &L.F064, &L.G164,
                  &L.A1, &L.G1, &L.G1T})
     bsr_free(*m);
-  for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u})
+  for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e})
     if (*v) { cudaFree(*v); *v = nullptr; }
 }
 
 void free_smoother(pum_hier* h) {
+  graph_destroy(h->vgraph);
   for (auto& L : h->lv) {
     for (Bsr* m : {&L.As, &L.PT, &L.Ps, &L.PTs, &L.G, &L.GT, &L.F0, &L.F0T, &L.G1, &L.G1T}) bsr_free(*m);
-    for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u})
+    for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e})
       if (*v) { cudaFree(*v); *v = nullptr; }
   }
   for (auto& w : h->w64)
@@ -143,7 +145,7 @@ void finalize_smoother(pum_ctx* ctx, pum_hier* h) {
       }
     }
     if (vdt == PUM_F32) bsr_convert(L.As, L.A, PUM_F32, s);
-    for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u}) *v = dalloc(vs * N);
+    for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e}) *v = dalloc(vs * N);
     PUM_CUDA(cudaMemsetAsync(L.x, 0, vs * N, s));
   }
   const size_t N0 = (size_t)h->lv[0].n * h->lv[0].d;
@@ -250,6 +252,8 @@ pum_status pum_create(pum_ctx** out, int device, void* cuda_stream) {
       PUM_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
       ctx->own_stream = true;
     }
+    const char* ng = getenv("PUM_NO_GRAPH");
+    ctx->graphs = !(ng && ng[0] == '1');
     ctx->status = (DevStatus*)dalloc(sizeof(DevStatus));
     ctx->scal = (double*)dalloc(sizeof(double) * kScalSlots);
     ctx->partials = (double*)dalloc(sizeof(double) * (1 << 16));
@@ -411,7 +415,7 @@ pum_status cheb4_smooth(pum_ctx* ctx, pum_hier* h, int level, const double* b, d
     const int64_t N = (int64_t)L.n * L.d;
     convert_vec(ctx, L.b, h->smooth_dt, b, PUM_F64, N);
     if (!x_is_zero) convert_vec(ctx, L.x, h->smooth_dt, x, PUM_F64, N);
-    cheb4(ctx, h, level, x_is_zero != 0);
+    cheb4(ctx, h, level, L.b, L.x, x_is_zero != 0, nullptr);
     convert_vec(ctx, x, PUM_F64, L.x, h->smooth_dt, N);
     return PUM_OK;
   });
@@ -683,6 +687,7 @@ pum_status pum_hier_load(pum_ctx* ctx, const char* path, pum_hier** out) {
 
 pum_status pum_hier_destroy(pum_hier* h) {
   if (!h) return PUM_ERR_INVALID_ARG;
+  graph_destroy(h->vgraph);
   for (auto& L : h->lv) free_level(L);
   for (auto& w : h->w64)
     if (w) cudaFree(w);

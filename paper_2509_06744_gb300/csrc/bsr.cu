@@ -47,23 +47,28 @@ template <typename T> __device__ __forceinline__ T from_acc(double v) { return (
 
 // ----------------------------------------------------------------------------- y = M x
 
-// One thread per output unknown (block row `row`, local index r).  The D threads of a
-// block row read the D rows of each d x d block (contiguous in the block-row-major
-// layout, so a block row's blocks are read as one contiguous stream) and the D values
-// of x of the block column (shared by the D threads).
+// G lanes per output unknown (block row `row`, local index r): lane g handles the blocks
+// b0 + g, b0 + g + G, ... of the block row and the G partial sums are combined with
+// warp shuffles.  The D x G lanes of a block row read the D rows of each d x d block
+// (contiguous: a block row's blocks are one contiguous stream) and the D values of x of
+// the block column.  G = 1 on fine levels (enough rows to fill the GPU); coarse levels,
+// with few rows and up to 25 blocks per row, use G up to 32 so that each lane walks only
+// one or two blocks instead of a 25-long chain of dependent loads.
 template <int D, typename MT, typename VT, int EPI>
-__global__ void __launch_bounds__(256) k_bsr_mv(int n_brows, int stride, const int* __restrict__ rp,
+__global__ void __launch_bounds__(256) k_bsr_mv(int n_brows, int stride, int lanes, const int* __restrict__ rp,
                                                 const int* __restrict__ ci, const MT* __restrict__ vals,
                                                 const VT* __restrict__ x, EpiArgs e) {
   using AT = typename AccOf<MT>::type;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t tid = gtid / lanes;  // output unknown
+  const int g = (int)(gtid - tid * lanes);
   const int row = (int)(tid / D);
   const int r = (int)(tid - (int64_t)row * D);
   const bool active = row < n_brows;
   AT acc = 0;
   if (active) {
     const int b0 = rp[row], b1 = rp[row + 1];
-    for (int b = b0; b < b1; ++b) {
+    for (int b = b0 + g; b < b1; b += lanes) {
       const int c = __ldg(ci + b);
       AT a[D], xv[D];
       load_row<D>(vals + (int64_t)b * stride + r * D, a);
@@ -72,10 +77,12 @@ __global__ void __launch_bounds__(256) k_bsr_mv(int n_brows, int stride, const i
       for (int q = 0; q < D; ++q) acc = fma(a[q], xv[q], acc);
     }
   }
+  for (int o = lanes >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, lanes);
+  const bool leader = active && g == 0;
   if constexpr (EPI == EPI_DOT) {
     __shared__ double red[256 / 32];
     double contrib = 0.0;
-    if (active) {
+    if (leader) {
       ((VT*)e.y)[tid] = (VT)acc;
       contrib = (double)acc * (double)x[tid];
     }
@@ -89,7 +96,7 @@ __global__ void __launch_bounds__(256) k_bsr_mv(int n_brows, int stride, const i
     }
     return;
   }
-  if (!active) return;
+  if (!leader) return;
   VT* y = (VT*)e.y;
   if constexpr (EPI == EPI_SET) {
     y[tid] = (VT)acc;
@@ -101,21 +108,31 @@ __global__ void __launch_bounds__(256) k_bsr_mv(int n_brows, int stride, const i
     VT* xo = (VT*)e.xo;
     y[tid] = (VT)acc;
     xo[tid] = (VT)((AT)e.dmu * acc);
+    if (e.xo2) ((VT*)e.xo2)[tid] = (VT)((AT)((VT*)e.xo2)[tid] + (AT)e.dmu * acc);
   } else if constexpr (EPI == EPI_CHEB_FIRST) {
     VT* xo = (VT*)e.xo;
     y[tid] = (VT)acc;
     xo[tid] = (VT)((AT)xo[tid] + (AT)e.dmu * acc);
+    if (e.xo2) ((VT*)e.xo2)[tid] = (VT)((AT)((VT*)e.xo2)[tid] + (AT)e.dmu * acc);
   } else if constexpr (EPI == EPI_CHEB) {
     VT* xo = (VT*)e.xo;
     AT pn = (AT)e.mu2 * (AT)y[tid] + acc;
     y[tid] = (VT)pn;
     xo[tid] = (VT)((AT)xo[tid] + (AT)e.dmu * pn);
+    if (e.xo2) ((VT*)e.xo2)[tid] = (VT)((AT)((VT*)e.xo2)[tid] + (AT)e.dmu * pn);
   }
 }
 
 template <int D, typename MT, typename VT>
 static void launch_mv_epi(pum_ctx* ctx, const Bsr& M, const void* x, int epi, const EpiArgs& e) {
-  const int64_t nthreads = (int64_t)M.n_brows * D;
+  // lanes per output: double while the GPU is not filled (about sm_count x 2048 resident
+  // threads) and a row still has blocks for the extra lane; the DOT epilogue's per-CTA
+  // partials assume one lane per output.
+  int lanes = 1;
+  if (epi != EPI_DOT)
+    while (lanes < 32 && (int64_t)M.n_brows * D * lanes < (int64_t)ctx->sm_count * 2048 && lanes < M.max_row_nnzb)
+      lanes *= 2;
+  const int64_t nthreads = (int64_t)M.n_brows * D * lanes;
   const int bs = 256;
   const unsigned grid = (unsigned)((nthreads + bs - 1) / bs);
   if (grid == 0) return;
@@ -124,7 +141,7 @@ static void launch_mv_epi(pum_ctx* ctx, const Bsr& M, const void* x, int epi, co
   cudaStream_t s = ctx->stream;
 #define PUM_MV_CASE(E)                                                                                \
   case E:                                                                                             \
-    k_bsr_mv<D, MT, VT, E><<<grid, bs, 0, s>>>(M.n_brows, M.stride, M.row_ptr, M.col_idx, v, xv, e); \
+    k_bsr_mv<D, MT, VT, E><<<grid, bs, 0, s>>>(M.n_brows, M.stride, lanes, M.row_ptr, M.col_idx, v, xv, e); \
     break;
   switch (epi) {
     PUM_MV_CASE(EPI_SET)
@@ -136,7 +153,7 @@ static void launch_mv_epi(pum_ctx* ctx, const Bsr& M, const void* x, int epi, co
     case EPI_DOT:
       if constexpr (std::is_same<MT, double>::value && std::is_same<VT, double>::value) {
         PUM_CHECK(grid <= (unsigned)(1 << 16), PUM_ERR_UNSUPPORTED, "dot epilogue: too many blocks");
-        k_bsr_mv<D, MT, VT, EPI_DOT><<<grid, bs, 0, s>>>(M.n_brows, M.stride, M.row_ptr, M.col_idx, v, xv, e);
+        k_bsr_mv<D, MT, VT, EPI_DOT><<<grid, bs, 0, s>>>(M.n_brows, M.stride, 1, M.row_ptr, M.col_idx, v, xv, e);
       } else {
         throw Error{PUM_ERR_UNSUPPORTED, "dot epilogue needs float64"};
       }
@@ -152,6 +169,8 @@ static void launch_mv_epi(pum_ctx* ctx, const Bsr& M, const void* x, int epi, co
 template <int D>
 static void launch_mv_d(pum_ctx* ctx, const Bsr& M, int vdt, const void* x, int epi, const EpiArgs& e) {
   if (M.dt == PUM_F64 && vdt == PUM_F64) return launch_mv_epi<D, double, double>(ctx, M, x, epi, e);
+  if (M.dt == PUM_F64 && vdt == PUM_F32 && epi == EPI_RESID)  // FP64 operator and sums on FP32 vectors
+    return launch_mv_epi<D, double, float>(ctx, M, x, epi, e);
   if (M.dt == PUM_F32 && vdt == PUM_F32) return launch_mv_epi<D, float, float>(ctx, M, x, epi, e);
   if (M.dt == PUM_BF16 && vdt == PUM_F32) return launch_mv_epi<D, __nv_bfloat16, float>(ctx, M, x, epi, e);
   throw Error{PUM_ERR_UNSUPPORTED, "bsr_mv: unsupported matrix/vector precision pair"};
@@ -274,6 +293,8 @@ void bsr_alloc(Bsr& m, int n_brows, int n_bcols, int d, int dt, const std::vecto
   m.nnzb = (int64_t)ci.size();
   m.h_row_ptr = rp;
   m.h_col_idx = ci;
+  m.max_row_nnzb = 0;
+  for (int i = 0; i < n_brows; ++i) m.max_row_nnzb = std::max(m.max_row_nnzb, rp[i + 1] - rp[i]);
   PUM_CHECK((int)rp.size() == n_brows + 1 && rp.back() == (int)ci.size(), PUM_ERR_INVALID_ARG, "bsr pattern");
   if (cudaMalloc(&m.row_ptr, sizeof(int) * rp.size()) != cudaSuccess ||
       cudaMalloc(&m.col_idx, sizeof(int) * std::max<size_t>(ci.size(), 1)) != cudaSuccess ||

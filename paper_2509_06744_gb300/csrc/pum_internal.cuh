@@ -65,6 +65,7 @@ inline int block_stride(int d, int dt) {
 
 struct Bsr {
   int n_brows = 0, n_bcols = 0, d = 0, stride = 0, dt = PUM_F64;
+  int max_row_nnzb = 0;  // longest block row
   int64_t nnzb = 0;
   int* row_ptr = nullptr;  // device
   int* col_idx = nullptr;  // device
@@ -111,12 +112,29 @@ struct Level {
   double logdet_S = 0.0;
   // work vectors in the smoothing precision
   void *x = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *t = nullptr, *u = nullptr;
+  void *c = nullptr, *e = nullptr;  // correction-form post-smoothing: rhs c = b - A x, iterate e
 };
 
 struct Coarse {
   int N = 0;
   double* L = nullptr;  // dense lower Cholesky factor, row-major N x N
 };
+
+// The V-cycle of a set-up hierarchy captured once as a CUDA graph and replayed.  When it
+// is captured with kernel timing on, the graph holds its own event pairs around every
+// finest-level kernel; their times are collected after each replay has completed.
+struct TimedEvent {
+  int tk;
+  cudaEvent_t start, stop;
+};
+struct GraphCache {
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;  // kernel launches per replay
+  bool timed = false;
+  bool pending = false;  // a timed replay whose events have not been collected
+  std::vector<TimedEvent> ev;
+};
+void graph_destroy(GraphCache& g);
 
 }  // namespace pum
 
@@ -131,6 +149,7 @@ struct pum_hier {
   std::vector<double> mu;  // Chebyshev mu_i, i = 1..k
   // FP64 work vectors of the finest level (PCG, conversions)
   double* w64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  pum::GraphCache vgraph;  // captured V-cycle
 };
 
 struct pum_ctx {
@@ -147,8 +166,10 @@ struct pum_ctx {
   bool timing = false;
   cudaEvent_t ev_pool[2][PUM_TK_COUNT];
   std::vector<cudaEvent_t> tk_start[PUM_TK_COUNT], tk_stop[PUM_TK_COUNT];
-  int64_t tk_launches[PUM_TK_COUNT] = {0, 0, 0, 0};
-  double tk_ms[PUM_TK_COUNT] = {0, 0, 0, 0};
+  int64_t tk_launches[PUM_TK_COUNT] = {};
+  double tk_ms[PUM_TK_COUNT] = {};
+  std::vector<pum::TimedEvent>* capture_ev = nullptr;  // set while a graph is being captured
+  bool graphs = true;                                   // capture the V-cycle when the stream allows it
 };
 
 namespace pum {
@@ -168,6 +189,7 @@ struct EpiArgs {
   void* xo;        // CHEB*: iterate updated in place
   double mu2;      // CHEB: p <- mu2 p + acc
   double dmu;      // CHEB*: x <- x + dmu p
+  void* xo2;       // CHEB*: optional second iterate updated the same way (x2 <- x2 + dmu p)
   double* partials;  // DOT: per-CTA partial sums of acc * x
 };
 
@@ -192,12 +214,14 @@ void coarse_factor(pum_ctx* ctx, pum_hier* h);
 
 // Smoother / cycle (solve.cu)
 void apply_M(pum_ctx* ctx, pum_hier* h, int l, const void* r, void* z, int tk_first);
-void cheb4(pum_ctx* ctx, pum_hier* h, int l, bool x_zero);
+void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_zero, void* x_acc);
 void vcycle_level(pum_ctx* ctx, pum_hier* h, int l);
 void coarse_solve(pum_ctx* ctx, pum_hier* h, const void* b, void* x, int vdt);
 
 inline void count_launch(pum_ctx* ctx) { ctx->launches++; }
 void timing_begin(pum_ctx* ctx, int tk);
 void timing_end(pum_ctx* ctx, int tk);
+// Collect the kernel times of the last timed graph replay (waits for it).
+void graph_harvest(pum_ctx* ctx, pum_hier* h);
 
 }  // namespace pum

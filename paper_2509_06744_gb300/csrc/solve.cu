@@ -11,6 +11,14 @@ namespace pum {
 
 void timing_begin(pum_ctx* ctx, int tk) {
   if (!ctx->timing) return;
+  if (ctx->capture_ev) {  // inside a graph capture: the graph gets its own event pair
+    TimedEvent t{tk, nullptr, nullptr};
+    PUM_CUDA(cudaEventCreate(&t.start));
+    PUM_CUDA(cudaEventCreate(&t.stop));
+    ctx->capture_ev->push_back(t);
+    PUM_CUDA(cudaEventRecordWithFlags(t.start, ctx->stream, cudaEventRecordExternal));  // a graph node
+    return;
+  }
   const size_t i = (size_t)ctx->tk_launches[tk];
   if (i >= ctx->tk_start[tk].size()) {
     cudaEvent_t a, b;
@@ -24,6 +32,10 @@ void timing_begin(pum_ctx* ctx, int tk) {
 
 void timing_end(pum_ctx* ctx, int tk) {
   if (!ctx->timing) return;
+  if (ctx->capture_ev) {
+    PUM_CUDA(cudaEventRecordWithFlags(ctx->capture_ev->back().stop, ctx->stream, cudaEventRecordExternal));
+    return;
+  }
   const size_t i = (size_t)ctx->tk_launches[tk];
   PUM_CUDA(cudaEventRecord(ctx->tk_stop[tk][i], ctx->stream));
   ctx->tk_launches[tk]++;
@@ -60,25 +72,27 @@ void apply_M(pum_ctx* ctx, pum_hier* h, int l, const void* r, void* z, int) {
   fsai_apply_epi(ctx, h, l, r, EPI_SET, e);
 }
 
-// Algorithm 3 on level l with right-hand side L.b and iterate L.x (in place).
-void cheb4(pum_ctx* ctx, pum_hier* h, int l, bool x_zero) {
+// Algorithm 3 on level l for A x = rhs with iterate x (in place); x_zero: x0 = 0.  When
+// x_acc is given, every update of x is also added to x_acc (the correction form below).
+void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_zero, void* x_acc) {
   Level& L = h->lv[l];
   const int vdt = h->smooth_dt;
   const int k = h->sp.degree_k;
   const double dd = 4.0 / L.beta;  // d = 4 / beta
   const bool fin = (l == 0);
   for (int i = 1; i <= k; ++i) {
-    const void* src = L.b;  // r = b when x0 = 0 on the first step
+    const void* src = rhs;  // r = b when x0 = 0 on the first step
     if (!(i == 1 && x_zero)) {
       EpiArgs e{};
       e.y = L.r;
-      e.b = L.b;
-      bsr_mv(ctx, smoothA(h, l), vdt, L.x, EPI_RESID, e, fin ? PUM_TK_RESID : -1);  // r = b - A x
+      e.b = rhs;
+      bsr_mv(ctx, smoothA(h, l), vdt, x, EPI_RESID, e, fin ? PUM_TK_RESID : -1);  // r = b - A x
       src = L.r;
     }
     EpiArgs e{};
     e.y = L.p;
-    e.xo = L.x;
+    e.xo = x;
+    e.xo2 = x_acc;
     e.dmu = dd * h->mu[i - 1];
     int epi;
     if (i == 1) {
@@ -128,6 +142,15 @@ void coarse_solve(pum_ctx* ctx, pum_hier* h, const void* b, void* x, int vdt) {
 
 // ----------------------------------------------------------------------------- V-cycle
 
+// One V(k,k) cycle from level l: L.x = B_l L.b.
+//
+// FP32 form (with resid_f64): Algorithm 3 is a polynomial method, x_k = x0 + q(MA) M (b - A x0),
+// so post-smoothing from x0 equals x0 plus post-smoothing of A e = c, c = b - A x0, from e0 = 0.
+// After the coarse correction x holds large smooth components, and an FP32 b - A x loses them
+// to cancellation (kappa(A) eps_32 >> 1 on the fine levels).  So c is formed once with the FP64
+// operator and FP64 sums, the FP32 smoother works on the small correction e, and every update of
+// e is also added to x in the same epilogue.  The residual restricted to the coarser level is
+// formed the same way.  In exact arithmetic this is the same cycle.
 void vcycle_level(pum_ctx* ctx, pum_hier* h, int l) {
   Level& L = h->lv[l];
   const int vdt = h->smooth_dt;
@@ -138,11 +161,14 @@ void vcycle_level(pum_ctx* ctx, pum_hier* h, int l) {
   Level& C = h->lv[l + 1];
   const Bsr& PT = vdt == PUM_F64 ? L.PT : L.PTs;
   const Bsr& P = vdt == PUM_F64 ? L.P : L.Ps;
-  cheb4(ctx, h, l, true);  // pre-smoothing from x0 = 0
+  const bool corr = vdt == PUM_F32 && h->sp.resid_f64;
+  const Bsr& Ar = corr ? L.A : smoothA(h, l);  // operator of the two accurate residuals
+  const int tk_r = l == 0 ? (corr ? PUM_TK_RESID64 : PUM_TK_RESID) : -1;
+  cheb4(ctx, h, l, L.b, L.x, true, nullptr);  // pre-smoothing from x0 = 0
   EpiArgs e{};
   e.y = L.r;
   e.b = L.b;
-  bsr_mv(ctx, smoothA(h, l), vdt, L.x, EPI_RESID, e, l == 0 ? PUM_TK_RESID : -1);  // r = b - A x
+  bsr_mv(ctx, Ar, vdt, L.x, EPI_RESID, e, tk_r);  // r = b - A x
   EpiArgs rs{};
   rs.y = C.b;
   bsr_mv(ctx, PT, vdt, L.r, EPI_SET, rs);  // b_c = P^T r
@@ -150,7 +176,15 @@ void vcycle_level(pum_ctx* ctx, pum_hier* h, int l) {
   EpiArgs pa{};
   pa.y = L.x;
   bsr_mv(ctx, P, vdt, C.x, EPI_ADD, pa);  // x += P x_c
-  cheb4(ctx, h, l, false);  // post-smoothing, same polynomial
+  if (!corr) {
+    cheb4(ctx, h, l, L.b, L.x, false, nullptr);  // post-smoothing, same polynomial
+    return;
+  }
+  EpiArgs cr{};
+  cr.y = L.c;
+  cr.b = L.b;
+  bsr_mv(ctx, Ar, vdt, L.x, EPI_RESID, cr, tk_r);  // c = b - A x
+  cheb4(ctx, h, l, L.c, L.e, true, L.x);         // A e = c from e0 = 0; x += each update
 }
 
 // ----------------------------------------------------------------------------- PCG
@@ -190,15 +224,80 @@ __global__ void k_pcg_p(double* __restrict__ p, const double* __restrict__ z, co
 
 __global__ void k_scal_move(double* scal, int dst, int src) { scal[dst] = scal[src]; }
 
+void graph_destroy(GraphCache& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto& t : g.ev) {
+    cudaEventDestroy(t.start);
+    cudaEventDestroy(t.stop);
+  }
+  g = GraphCache();
+}
+
+void graph_harvest(pum_ctx* ctx, pum_hier* h) {
+  GraphCache& g = h->vgraph;
+  if (!g.pending) return;
+  g.pending = false;
+  for (auto& t : g.ev) {
+    PUM_CUDA(cudaEventSynchronize(t.stop));
+    float ms = 0.f;
+    PUM_CUDA(cudaEventElapsedTime(&ms, t.start, t.stop));
+    ctx->tk_ms[t.tk] += ms;
+    ctx->tk_launches[t.tk]++;
+  }
+}
+
+// Streams a graph can be captured on: not the legacy or per-thread default streams.
+static bool capturable(pum_ctx* ctx) {
+  const uintptr_t s = (uintptr_t)ctx->stream;
+  return ctx->graphs && s > 2;
+}
+
+static void build_vcycle_graph(pum_ctx* ctx, pum_hier* h) {
+  GraphCache& g = h->vgraph;
+  graph_destroy(g);
+  cudaGraph_t graph = nullptr;
+  const int64_t l0 = ctx->launches;
+  PUM_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  ctx->capture_ev = &g.ev;
+  try {
+    vcycle_level(ctx, h, 0);
+  } catch (...) {
+    ctx->capture_ev = nullptr;
+    cudaStreamEndCapture(ctx->stream, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    ctx->launches = l0;
+    throw;
+  }
+  ctx->capture_ev = nullptr;
+  PUM_CUDA(cudaStreamEndCapture(ctx->stream, &graph));
+  g.kernels = ctx->launches - l0;
+  ctx->launches = l0;  // counted per replay
+  const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  PUM_CUDA(e);
+  g.timed = ctx->timing;
+}
+
 static void vcycle64(pum_ctx* ctx, pum_hier* h, const double* r, double* z) {
   Level& L0 = h->lv[0];
   const int64_t N = (int64_t)L0.n * L0.d;
   convert_vec(ctx, L0.b, h->smooth_dt, r, PUM_F64, N);
-  vcycle_level(ctx, h, 0);
+  if (capturable(ctx)) {
+    graph_harvest(ctx, h);
+    if (!h->vgraph.exec || h->vgraph.timed != ctx->timing) build_vcycle_graph(ctx, h);
+    PUM_CUDA(cudaGraphLaunch(h->vgraph.exec, ctx->stream));
+    ctx->launches += h->vgraph.kernels;
+    h->vgraph.pending = h->vgraph.timed;
+  } else {
+    vcycle_level(ctx, h, 0);
+  }
   convert_vec(ctx, z, PUM_F64, L0.x, h->smooth_dt, N);
 }
 
-void vcycle_apply_impl(pum_ctx* ctx, pum_hier* h, const double* r, double* z) { vcycle64(ctx, h, r, z); }
+void vcycle_apply_impl(pum_ctx* ctx, pum_hier* h, const double* r, double* z) {
+  vcycle64(ctx, h, r, z);
+  if (ctx->timing) graph_harvest(ctx, h);  // timing mode: collect before returning
+}
 
 pum_status pcg_impl(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_report* rep) {
   Level& L0 = h->lv[0];
@@ -249,6 +348,7 @@ pum_status pcg_impl(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_r
     rep->final_relres = rel;
     if (rel <= rep->rtol) {
       rep->converged = 1;
+      graph_harvest(ctx, h);
       return PUM_OK;
     }
     if (rep->flexible) PUM_CUDA(cudaMemcpyAsync(zo, z, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
@@ -260,6 +360,7 @@ pum_status pcg_impl(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_r
     ctx->launches += 2;
     PUM_CUDA(cudaGetLastError());
   }
+  graph_harvest(ctx, h);
   return PUM_ERR_NOCONV;
 }
 

@@ -338,3 +338,29 @@ def test_indefinite_matrix_reports_not_spd(lib, ctx):
         H.setup(p0="lower", k=2)
     assert e.value.status == 4
     ctx.sync()  # the context stays usable
+
+
+def test_graph_replay_is_bitwise_identical(lib, small_biharmonic):
+    """On a capturable stream the V-cycle is replayed from a CUDA graph: same bits as direct launches."""
+    import torch
+    h = small_biharmonic
+    s = torch.cuda.Stream()
+    outs = []
+    for stream in (None, s):
+        with torch.cuda.stream(s if stream is not None else torch.cuda.current_stream()):
+            c = lib.Context(0, stream=stream.cuda_stream if stream is not None else None)
+            H = hier_from_oracle(lib, c, h)
+            H.setup(p0="lower", adaptive=False, k=PR.cheb_k)
+            r = cuda(pin.normal_vector(PR.n_dofs, 5))
+            z1, z2 = torch.zeros_like(r), torch.zeros_like(r)
+            H.vcycle(r, z1)
+            H.vcycle(r, z2)  # second call replays the captured graph
+            x = torch.zeros_like(r)
+            rep = H.pcg(cuda(h.b), x, rtol=1e-8, maxit=100)
+            torch.cuda.synchronize()
+            outs.append((host(z1), host(z2), host(x), rep["history"]))
+            H.close()
+            c.close()
+    (a1, a2, ax, ah), (b1, b2, bx, bh) = outs
+    assert np.array_equal(a1, b1) and np.array_equal(a2, b2) and np.array_equal(a1, a2)
+    assert np.array_equal(ax, bx) and ah == bh
