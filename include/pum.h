@@ -103,8 +103,11 @@ typedef struct {
   uint64_t lanczos_seed; /* SplitMix64 seed of the start vector; level l uses seed + l     */
   int32_t smooth_dt;     /* PUM_F64 or PUM_F32: storage and arithmetic of A, P and vectors  */
   int32_t g_dt;          /* PUM_F64, PUM_F32 or PUM_BF16 (BF16 needs smooth_dt = PUM_F32)   */
-  int32_t resid_f64;     /* FP32 form: 1 forms the residual restricted to the next level with
-                            the FP64 operator and FP64 sums (vectors stay FP32)              */
+  int32_t mixed_levels;  /* FP32 form: the first mixed_levels levels keep their iterate and
+                            right-hand side in FP64 (FP32 smoothing of corrections, residuals
+                            with the FP64 operator, FP64 prolongation between such levels);
+                            with mixed_levels > 0 the other levels post-smooth in correction
+                            form with FP64-operator residuals; 0: plain FP32 cycle           */
 } smoother_params;
 
 /* Outer preconditioned CG (one V(k,k) cycle as preconditioner). */

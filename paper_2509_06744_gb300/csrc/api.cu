@@ -59,7 +59,7 @@ void free_level(Level& L) {
   for (Bsr* m : {&L.A, &L.As, &L.P, &L.PT, &L.Ps, &L.PTs, &L.G, &L.GT, &L.G64, &L.F0, &L.F0T, &L.F064, &L.G164,
                  &L.A1, &L.G1, &L.G1T})
     bsr_free(*m);
-  for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e})
+  for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e, (void**)&L.b64, (void**)&L.z64})
     if (*v) { cudaFree(*v); *v = nullptr; }
 }
 
@@ -67,7 +67,7 @@ void free_smoother(pum_hier* h) {
   graph_destroy(h->vgraph);
   for (auto& L : h->lv) {
     for (Bsr* m : {&L.As, &L.PT, &L.Ps, &L.PTs, &L.G, &L.GT, &L.F0, &L.F0T, &L.G1, &L.G1T}) bsr_free(*m);
-    for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e})
+    for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e, (void**)&L.b64, (void**)&L.z64})
       if (*v) { cudaFree(*v); *v = nullptr; }
   }
   for (auto& w : h->w64)
@@ -146,6 +146,10 @@ void finalize_smoother(pum_ctx* ctx, pum_hier* h) {
     }
     if (vdt == PUM_F32) bsr_convert(L.As, L.A, PUM_F32, s);
     for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e}) *v = dalloc(vs * N);
+    if (vdt == PUM_F32 && l > 0 && (l < h->sp.mixed_levels || l == nl - 1)) {
+      L.b64 = (double*)dalloc(sizeof(double) * N);
+      L.z64 = (double*)dalloc(sizeof(double) * N);
+    }
     PUM_CUDA(cudaMemsetAsync(L.x, 0, vs * N, s));
   }
   const size_t N0 = (size_t)h->lv[0].n * h->lv[0].d;
@@ -168,6 +172,7 @@ void check_params(const bfsai_params* fp, const smoother_params* sp) {
   PUM_CHECK(fp->tie_rel >= 0.0, PUM_ERR_INVALID_ARG, "tie_rel must be >= 0");
   PUM_CHECK(sp->degree_k >= 1 && sp->degree_k <= 64, PUM_ERR_INVALID_ARG, "degree_k must be in 1..64");
   PUM_CHECK(sp->lanczos_its >= 1 && sp->lanczos_safety >= 1.0, PUM_ERR_INVALID_ARG, "Lanczos parameters");
+  PUM_CHECK(sp->mixed_levels >= 0, PUM_ERR_INVALID_ARG, "mixed_levels must be >= 0");
   PUM_CHECK(sp->smooth_dt == PUM_F64 || sp->smooth_dt == PUM_F32, PUM_ERR_INVALID_ARG, "smooth_dt must be F64 or F32");
   PUM_CHECK(sp->g_dt == PUM_F64 || sp->g_dt == PUM_F32 || sp->g_dt == PUM_BF16, PUM_ERR_INVALID_ARG, "g_dt");
   PUM_CHECK(!(sp->smooth_dt == PUM_F64 && sp->g_dt != PUM_F64), PUM_ERR_INVALID_ARG,
@@ -415,7 +420,7 @@ pum_status cheb4_smooth(pum_ctx* ctx, pum_hier* h, int level, const double* b, d
     const int64_t N = (int64_t)L.n * L.d;
     convert_vec(ctx, L.b, h->smooth_dt, b, PUM_F64, N);
     if (!x_is_zero) convert_vec(ctx, L.x, h->smooth_dt, x, PUM_F64, N);
-    cheb4(ctx, h, level, L.b, L.x, x_is_zero != 0, nullptr);
+    cheb4(ctx, h, level, L.b, L.x, x_is_zero != 0, nullptr, -1, false);
     convert_vec(ctx, x, PUM_F64, L.x, h->smooth_dt, N);
     return PUM_OK;
   });
@@ -709,6 +714,7 @@ pum_status pum_timing_reset(pum_ctx* ctx) {
     for (int k = 0; k < PUM_TK_COUNT; ++k) {
       ctx->tk_launches[k] = 0;
       ctx->tk_ms[k] = 0.0;
+      ctx->tk_pool_used[k] = 0;
     }
     return PUM_OK;
   });
@@ -719,14 +725,16 @@ pum_status pum_timing_read(pum_ctx* ctx, int64_t* launches, double* ms) {
   return guard(ctx, [&]() {
     PUM_CUDA(cudaStreamSynchronize(ctx->stream));
     for (int k = 0; k < PUM_TK_COUNT; ++k) {
-      double tot = 0.0;
-      for (int64_t i = 0; i < ctx->tk_launches[k]; ++i) {
+      // collect the direct launches' event pairs (graph replays are collected as they finish)
+      for (int64_t i = 0; i < ctx->tk_pool_used[k]; ++i) {
         float t = 0.f;
         PUM_CUDA(cudaEventElapsedTime(&t, ctx->tk_start[k][i], ctx->tk_stop[k][i]));
-        tot += t;
+        ctx->tk_ms[k] += t;
+        ctx->tk_launches[k]++;
       }
+      ctx->tk_pool_used[k] = 0;
       launches[k] = ctx->tk_launches[k];
-      ms[k] = tot;
+      ms[k] = ctx->tk_ms[k];
     }
     return PUM_OK;
   });

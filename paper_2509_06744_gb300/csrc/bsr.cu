@@ -54,10 +54,10 @@ template <typename T> __device__ __forceinline__ T from_acc(double v) { return (
 // the block column.  G = 1 on fine levels (enough rows to fill the GPU); coarse levels,
 // with few rows and up to 25 blocks per row, use G up to 32 so that each lane walks only
 // one or two blocks instead of a 25-long chain of dependent loads.
-template <int D, typename MT, typename VT, int EPI>
+template <int D, typename MT, typename XT, typename YT, typename X2T, int EPI>
 __global__ void __launch_bounds__(256) k_bsr_mv(int n_brows, int stride, int lanes, const int* __restrict__ rp,
                                                 const int* __restrict__ ci, const MT* __restrict__ vals,
-                                                const VT* __restrict__ x, EpiArgs e) {
+                                                const XT* __restrict__ x, EpiArgs e) {
   using AT = typename AccOf<MT>::type;
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t tid = gtid / lanes;  // output unknown
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) k_bsr_mv(int n_brows, int stride, int lan
     __shared__ double red[256 / 32];
     double contrib = 0.0;
     if (leader) {
-      ((VT*)e.y)[tid] = (VT)acc;
+      ((YT*)e.y)[tid] = (YT)acc;
       contrib = (double)acc * (double)x[tid];
     }
     for (int o = 16; o > 0; o >>= 1) contrib += __shfl_down_sync(0xffffffffu, contrib, o);
@@ -97,33 +97,41 @@ __global__ void __launch_bounds__(256) k_bsr_mv(int n_brows, int stride, int lan
     return;
   }
   if (!leader) return;
-  VT* y = (VT*)e.y;
+  YT* y = (YT*)e.y;
+  X2T* x2 = (X2T*)e.xo2;
   if constexpr (EPI == EPI_SET) {
-    y[tid] = (VT)acc;
+    y[tid] = (YT)acc;
   } else if constexpr (EPI == EPI_RESID) {
-    y[tid] = (VT)((AT)((const VT*)e.b)[tid] - acc);
+    // b - A x, formed in the accumulation precision (FP64 for an FP64 operator)
+    y[tid] = (YT)((AT)((const XT*)e.b)[tid] - acc);
   } else if constexpr (EPI == EPI_ADD) {
-    y[tid] = (VT)((AT)y[tid] + acc);
+    y[tid] = (YT)((AT)y[tid] + acc);
   } else if constexpr (EPI == EPI_CHEB_FIRST0) {
-    VT* xo = (VT*)e.xo;
-    y[tid] = (VT)acc;
-    xo[tid] = (VT)((AT)e.dmu * acc);
-    if (e.xo2) ((VT*)e.xo2)[tid] = (VT)((AT)((VT*)e.xo2)[tid] + (AT)e.dmu * acc);
+    YT* xo = (YT*)e.xo;
+    y[tid] = (YT)acc;
+    xo[tid] = (YT)((AT)e.dmu * acc);
+    if (x2) x2[tid] = e.x2_set ? (X2T)(e.dmu * (double)acc) : (X2T)((double)x2[tid] + e.dmu * (double)acc);
   } else if constexpr (EPI == EPI_CHEB_FIRST) {
-    VT* xo = (VT*)e.xo;
-    y[tid] = (VT)acc;
-    xo[tid] = (VT)((AT)xo[tid] + (AT)e.dmu * acc);
-    if (e.xo2) ((VT*)e.xo2)[tid] = (VT)((AT)((VT*)e.xo2)[tid] + (AT)e.dmu * acc);
+    YT* xo = (YT*)e.xo;
+    y[tid] = (YT)acc;
+    xo[tid] = (YT)((AT)xo[tid] + (AT)e.dmu * acc);
+    if (x2) x2[tid] = (X2T)((double)x2[tid] + e.dmu * (double)acc);
   } else if constexpr (EPI == EPI_CHEB) {
-    VT* xo = (VT*)e.xo;
-    AT pn = (AT)e.mu2 * (AT)y[tid] + acc;
-    y[tid] = (VT)pn;
-    xo[tid] = (VT)((AT)xo[tid] + (AT)e.dmu * pn);
-    if (e.xo2) ((VT*)e.xo2)[tid] = (VT)((AT)((VT*)e.xo2)[tid] + (AT)e.dmu * pn);
+    YT* xo = (YT*)e.xo;
+    const AT pn = (AT)e.mu2 * (AT)y[tid] + acc;
+    y[tid] = (YT)pn;
+    xo[tid] = (YT)((AT)xo[tid] + (AT)e.dmu * pn);
+    if (x2) x2[tid] = (X2T)((double)x2[tid] + e.dmu * (double)pn);
   }
 }
 
-template <int D, typename MT, typename VT>
+// Epilogue sets a type combination is instantiated for.
+constexpr unsigned kAllEpi = 0x7Fu;
+constexpr unsigned kResidOnly = 1u << EPI_RESID;
+constexpr unsigned kAddOnly = 1u << EPI_ADD;
+constexpr unsigned kChebOnly = (1u << EPI_CHEB_FIRST0) | (1u << EPI_CHEB_FIRST) | (1u << EPI_CHEB);
+
+template <int D, typename MT, typename XT, typename YT, typename X2T, unsigned EPIS>
 static void launch_mv_epi(pum_ctx* ctx, const Bsr& M, const void* x, int epi, const EpiArgs& e) {
   // lanes per output: double while the GPU is not filled (about sm_count x 2048 resident
   // threads) and a row still has blocks for the extra lane; the DOT epilogue's per-CTA
@@ -137,11 +145,14 @@ static void launch_mv_epi(pum_ctx* ctx, const Bsr& M, const void* x, int epi, co
   const unsigned grid = (unsigned)((nthreads + bs - 1) / bs);
   if (grid == 0) return;
   auto* v = (const MT*)M.vals;
-  auto* xv = (const VT*)x;
+  auto* xv = (const XT*)x;
   cudaStream_t s = ctx->stream;
-#define PUM_MV_CASE(E)                                                                                \
-  case E:                                                                                             \
-    k_bsr_mv<D, MT, VT, E><<<grid, bs, 0, s>>>(M.n_brows, M.stride, lanes, M.row_ptr, M.col_idx, v, xv, e); \
+  PUM_CHECK((EPIS >> epi) & 1u, PUM_ERR_UNSUPPORTED, "bsr_mv: epilogue not available for this precision mix");
+#define PUM_MV_CASE(E)                                                                                            \
+  case E:                                                                                                         \
+    if constexpr ((EPIS >> E) & 1u)                                                                               \
+      k_bsr_mv<D, MT, XT, YT, X2T, E><<<grid, bs, 0, s>>>(M.n_brows, M.stride, lanes, M.row_ptr, M.col_idx, v, xv, \
+                                                          e);                                                     \
     break;
   switch (epi) {
     PUM_MV_CASE(EPI_SET)
@@ -151,9 +162,11 @@ static void launch_mv_epi(pum_ctx* ctx, const Bsr& M, const void* x, int epi, co
     PUM_MV_CASE(EPI_CHEB_FIRST)
     PUM_MV_CASE(EPI_CHEB)
     case EPI_DOT:
-      if constexpr (std::is_same<MT, double>::value && std::is_same<VT, double>::value) {
+      if constexpr (std::is_same<MT, double>::value && std::is_same<XT, double>::value &&
+                    std::is_same<YT, double>::value && ((EPIS >> EPI_DOT) & 1u)) {
         PUM_CHECK(grid <= (unsigned)(1 << 16), PUM_ERR_UNSUPPORTED, "dot epilogue: too many blocks");
-        k_bsr_mv<D, MT, VT, EPI_DOT><<<grid, bs, 0, s>>>(M.n_brows, M.stride, 1, M.row_ptr, M.col_idx, v, xv, e);
+        k_bsr_mv<D, MT, XT, YT, X2T, EPI_DOT><<<grid, bs, 0, s>>>(M.n_brows, M.stride, 1, M.row_ptr, M.col_idx, v,
+                                                                 xv, e);
       } else {
         throw Error{PUM_ERR_UNSUPPORTED, "dot epilogue needs float64"};
       }
@@ -168,12 +181,30 @@ static void launch_mv_epi(pum_ctx* ctx, const Bsr& M, const void* x, int epi, co
 
 template <int D>
 static void launch_mv_d(pum_ctx* ctx, const Bsr& M, int vdt, const void* x, int epi, const EpiArgs& e) {
-  if (M.dt == PUM_F64 && vdt == PUM_F64) return launch_mv_epi<D, double, double>(ctx, M, x, epi, e);
-  if (M.dt == PUM_F64 && vdt == PUM_F32 && epi == EPI_RESID)  // FP64 operator and sums on FP32 vectors
-    return launch_mv_epi<D, double, float>(ctx, M, x, epi, e);
-  if (M.dt == PUM_F32 && vdt == PUM_F32) return launch_mv_epi<D, float, float>(ctx, M, x, epi, e);
-  if (M.dt == PUM_BF16 && vdt == PUM_F32) return launch_mv_epi<D, __nv_bfloat16, float>(ctx, M, x, epi, e);
-  throw Error{PUM_ERR_UNSUPPORTED, "bsr_mv: unsupported matrix/vector precision pair"};
+  const int xdt = e.xdt >= 0 ? e.xdt : vdt;
+  const int ydt = e.ydt >= 0 ? e.ydt : vdt;
+  const int x2dt = (e.xo2 && e.x2dt >= 0) ? e.x2dt : ydt;
+  const int mdt = M.dt;
+  if (mdt == PUM_F64 && xdt == PUM_F64 && ydt == PUM_F64 && x2dt == PUM_F64)
+    return launch_mv_epi<D, double, double, double, double, kAllEpi>(ctx, M, x, epi, e);
+  if (mdt == PUM_F32 && xdt == PUM_F32 && ydt == PUM_F32 && x2dt == PUM_F32)
+    return launch_mv_epi<D, float, float, float, float, kAllEpi & ~(1u << EPI_DOT)>(ctx, M, x, epi, e);
+  if (mdt == PUM_BF16 && xdt == PUM_F32 && ydt == PUM_F32 && x2dt == PUM_F32)
+    return launch_mv_epi<D, __nv_bfloat16, float, float, float, kAllEpi & ~(1u << EPI_DOT)>(ctx, M, x, epi, e);
+  // FP32 smoother accumulating its updates into an FP64 iterate
+  if (mdt == PUM_F32 && xdt == PUM_F32 && ydt == PUM_F32 && x2dt == PUM_F64)
+    return launch_mv_epi<D, float, float, float, double, kChebOnly>(ctx, M, x, epi, e);
+  if (mdt == PUM_BF16 && xdt == PUM_F32 && ydt == PUM_F32 && x2dt == PUM_F64)
+    return launch_mv_epi<D, __nv_bfloat16, float, float, double, kChebOnly>(ctx, M, x, epi, e);
+  // residuals with the FP64 operator and FP64 sums, FP32 result
+  if (mdt == PUM_F64 && xdt == PUM_F32 && ydt == PUM_F32)
+    return launch_mv_epi<D, double, float, float, float, kResidOnly>(ctx, M, x, epi, e);
+  if (mdt == PUM_F64 && xdt == PUM_F64 && ydt == PUM_F32)
+    return launch_mv_epi<D, double, double, float, float, kResidOnly>(ctx, M, x, epi, e);
+  // FP32 prolongation added into an FP64 iterate
+  if (mdt == PUM_F32 && xdt == PUM_F32 && ydt == PUM_F64)
+    return launch_mv_epi<D, float, float, double, double, kAddOnly>(ctx, M, x, epi, e);
+  throw Error{PUM_ERR_UNSUPPORTED, "bsr_mv: unsupported matrix/vector precision mix"};
 }
 
 unsigned mv_grid_blocks(const Bsr& M) { return (unsigned)(((int64_t)M.n_brows * M.d + 255) / 256); }

@@ -113,6 +113,7 @@ struct Level {
   // work vectors in the smoothing precision
   void *x = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *t = nullptr, *u = nullptr;
   void *c = nullptr, *e = nullptr;  // correction-form post-smoothing: rhs c = b - A x, iterate e
+  double *b64 = nullptr, *z64 = nullptr;  // FP64 right-hand side and iterate of a mixed level
 };
 
 struct Coarse {
@@ -133,6 +134,8 @@ struct GraphCache {
   bool timed = false;
   bool pending = false;  // a timed replay whose events have not been collected
   std::vector<TimedEvent> ev;
+  const double* r = nullptr;  // vectors the graph was captured for
+  double* z = nullptr;
 };
 void graph_destroy(GraphCache& g);
 
@@ -166,8 +169,9 @@ struct pum_ctx {
   bool timing = false;
   cudaEvent_t ev_pool[2][PUM_TK_COUNT];
   std::vector<cudaEvent_t> tk_start[PUM_TK_COUNT], tk_stop[PUM_TK_COUNT];
-  int64_t tk_launches[PUM_TK_COUNT] = {};
-  double tk_ms[PUM_TK_COUNT] = {};
+  int64_t tk_launches[PUM_TK_COUNT] = {};  // launches timed since the last reset (collected)
+  double tk_ms[PUM_TK_COUNT] = {};         // their summed event time
+  int64_t tk_pool_used[PUM_TK_COUNT] = {}; // event pairs of direct launches not yet collected
   std::vector<pum::TimedEvent>* capture_ev = nullptr;  // set while a graph is being captured
   bool graphs = true;                                   // capture the V-cycle when the stream allows it
 };
@@ -184,13 +188,15 @@ enum Epi { EPI_SET = 0, EPI_RESID = 1, EPI_ADD = 2, EPI_CHEB_FIRST0 = 3, EPI_CHE
            EPI_DOT = 6 };
 
 struct EpiArgs {
-  void* y;         // output (SET/RESID/ADD/DOT) or p (CHEB*)
-  const void* b;   // RESID: right-hand side
-  void* xo;        // CHEB*: iterate updated in place
-  double mu2;      // CHEB: p <- mu2 p + acc
-  double dmu;      // CHEB*: x <- x + dmu p
-  void* xo2;       // CHEB*: optional second iterate updated the same way (x2 <- x2 + dmu p)
-  double* partials;  // DOT: per-CTA partial sums of acc * x
+  void* y = nullptr;         // output (SET/RESID/ADD/DOT) or p (CHEB*)
+  const void* b = nullptr;   // RESID: right-hand side (same type as the input vector x)
+  void* xo = nullptr;        // CHEB*: iterate updated in place (same type as y)
+  double mu2 = 0.0;          // CHEB: p <- mu2 p + acc
+  double dmu = 0.0;          // CHEB*: x <- x + dmu p
+  void* xo2 = nullptr;       // CHEB*: optional second iterate updated the same way (x2 <- x2 + dmu p)
+  bool x2_set = false;       // CHEB_FIRST0: x2 <- dmu p instead of x2 += dmu p
+  double* partials = nullptr;  // DOT: per-CTA partial sums of acc * x
+  int xdt = -1, ydt = -1, x2dt = -1;  // vector dtypes when they differ from the call's vdt
 };
 
 // y (by epilogue) = M x for a BSR matrix; vector dtype vdt (F64 or F32).
@@ -214,7 +220,8 @@ void coarse_factor(pum_ctx* ctx, pum_hier* h);
 
 // Smoother / cycle (solve.cu)
 void apply_M(pum_ctx* ctx, pum_hier* h, int l, const void* r, void* z, int tk_first);
-void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_zero, void* x_acc);
+void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_zero, void* x_acc, int acc_dt,
+           bool acc_set);
 void vcycle_level(pum_ctx* ctx, pum_hier* h, int l);
 void coarse_solve(pum_ctx* ctx, pum_hier* h, const void* b, void* x, int vdt);
 

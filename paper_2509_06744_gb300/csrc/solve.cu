@@ -19,7 +19,7 @@ void timing_begin(pum_ctx* ctx, int tk) {
     PUM_CUDA(cudaEventRecordWithFlags(t.start, ctx->stream, cudaEventRecordExternal));  // a graph node
     return;
   }
-  const size_t i = (size_t)ctx->tk_launches[tk];
+  const size_t i = (size_t)ctx->tk_pool_used[tk];
   if (i >= ctx->tk_start[tk].size()) {
     cudaEvent_t a, b;
     PUM_CUDA(cudaEventCreate(&a));
@@ -36,9 +36,9 @@ void timing_end(pum_ctx* ctx, int tk) {
     PUM_CUDA(cudaEventRecordWithFlags(ctx->capture_ev->back().stop, ctx->stream, cudaEventRecordExternal));
     return;
   }
-  const size_t i = (size_t)ctx->tk_launches[tk];
+  const size_t i = (size_t)ctx->tk_pool_used[tk];
   PUM_CUDA(cudaEventRecord(ctx->tk_stop[tk][i], ctx->stream));
-  ctx->tk_launches[tk]++;
+  ctx->tk_pool_used[tk]++;
 }
 
 // ----------------------------------------------------------------------------- smoother
@@ -74,7 +74,8 @@ void apply_M(pum_ctx* ctx, pum_hier* h, int l, const void* r, void* z, int) {
 
 // Algorithm 3 on level l for A x = rhs with iterate x (in place); x_zero: x0 = 0.  When
 // x_acc is given, every update of x is also added to x_acc (the correction form below).
-void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_zero, void* x_acc) {
+void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_zero, void* x_acc, int acc_dt,
+           bool acc_set) {
   Level& L = h->lv[l];
   const int vdt = h->smooth_dt;
   const int k = h->sp.degree_k;
@@ -93,6 +94,8 @@ void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_ze
     e.y = L.p;
     e.xo = x;
     e.xo2 = x_acc;
+    e.x2dt = acc_dt;
+    e.x2_set = acc_set && x_zero && i == 1;
     e.dmu = dd * h->mu[i - 1];
     int epi;
     if (i == 1) {
@@ -144,7 +147,7 @@ void coarse_solve(pum_ctx* ctx, pum_hier* h, const void* b, void* x, int vdt) {
 
 // One V(k,k) cycle from level l: L.x = B_l L.b.
 //
-// FP32 form (with resid_f64): Algorithm 3 is a polynomial method, x_k = x0 + q(MA) M (b - A x0),
+// FP32 form with mixed_levels > 0: Algorithm 3 is a polynomial method, x_k = x0 + q(MA) M (b - A x0),
 // so post-smoothing from x0 equals x0 plus post-smoothing of A e = c, c = b - A x0, from e0 = 0.
 // After the coarse correction x holds large smooth components, and an FP32 b - A x loses them
 // to cancellation (kappa(A) eps_32 >> 1 on the fine levels).  So c is formed once with the FP64
@@ -161,10 +164,10 @@ void vcycle_level(pum_ctx* ctx, pum_hier* h, int l) {
   Level& C = h->lv[l + 1];
   const Bsr& PT = vdt == PUM_F64 ? L.PT : L.PTs;
   const Bsr& P = vdt == PUM_F64 ? L.P : L.Ps;
-  const bool corr = vdt == PUM_F32 && h->sp.resid_f64;
+  const bool corr = vdt == PUM_F32 && h->sp.mixed_levels > 0;
   const Bsr& Ar = corr ? L.A : smoothA(h, l);  // operator of the two accurate residuals
   const int tk_r = l == 0 ? (corr ? PUM_TK_RESID64 : PUM_TK_RESID) : -1;
-  cheb4(ctx, h, l, L.b, L.x, true, nullptr);  // pre-smoothing from x0 = 0
+  cheb4(ctx, h, l, L.b, L.x, true, nullptr, -1, false);  // pre-smoothing from x0 = 0
   EpiArgs e{};
   e.y = L.r;
   e.b = L.b;
@@ -177,14 +180,14 @@ void vcycle_level(pum_ctx* ctx, pum_hier* h, int l) {
   pa.y = L.x;
   bsr_mv(ctx, P, vdt, C.x, EPI_ADD, pa);  // x += P x_c
   if (!corr) {
-    cheb4(ctx, h, l, L.b, L.x, false, nullptr);  // post-smoothing, same polynomial
+    cheb4(ctx, h, l, L.b, L.x, false, nullptr, -1, false);  // post-smoothing, same polynomial
     return;
   }
   EpiArgs cr{};
   cr.y = L.c;
   cr.b = L.b;
   bsr_mv(ctx, Ar, vdt, L.x, EPI_RESID, cr, tk_r);  // c = b - A x
-  cheb4(ctx, h, l, L.c, L.e, true, L.x);         // A e = c from e0 = 0; x += each update
+  cheb4(ctx, h, l, L.c, L.e, true, L.x, -1, false);  // A e = c from e0 = 0; x += each update
 }
 
 // ----------------------------------------------------------------------------- PCG
@@ -252,7 +255,72 @@ static bool capturable(pum_ctx* ctx) {
   return ctx->graphs && s > 2;
 }
 
-static void build_vcycle_graph(pum_ctx* ctx, pum_hier* h) {
+// Mixed levels of the FP32 form (l < mixed_levels): the level's iterate z and right-hand
+// side r stay in FP64.  The FP32 smoother works on correction vectors (pre-smoothing from
+// zero, post-smoothing of A e = c) and its fused epilogue adds every update to z in FP64,
+// so z carries no FP32 rounding: A times an FP32 rounding of a smooth z would be
+// kappa * eps_32 times larger than a smooth residual.  Both residuals use the FP64
+// operator on the FP64 z and r; the coarse correction of a mixed coarser level is
+// prolongated with the FP64 P.  In exact arithmetic this is the same V(k,k) cycle.
+static bool is_mixed(const pum_hier* h, int l) {
+  return h->smooth_dt == PUM_F32 && l < h->sp.mixed_levels;
+}
+
+static void vcycle_mixed(pum_ctx* ctx, pum_hier* h, int l, const double* r, double* z) {
+  Level& L = h->lv[l];
+  const int64_t N = (int64_t)L.n * L.d;
+  if (l == (int)h->lv.size() - 1) {
+    coarse_solve(ctx, h, r, z, PUM_F64);
+    return;
+  }
+  Level& C = h->lv[l + 1];
+  const int tk = l == 0 ? PUM_TK_RESID64 : -1;
+  convert_vec(ctx, L.b, PUM_F32, r, PUM_F64, N);       // FP32 right-hand side of the smoother
+  cheb4(ctx, h, l, L.b, L.e, true, z, PUM_F64, true);  // pre-smoothing: z = e in FP64
+  EpiArgs er{};
+  er.y = L.r;
+  er.b = r;
+  er.xdt = PUM_F64;
+  er.ydt = PUM_F32;
+  bsr_mv(ctx, L.A, PUM_F32, z, EPI_RESID, er, tk);  // r_f = r - A z
+  EpiArgs rs{};
+  rs.y = C.b;
+  bsr_mv(ctx, L.PTs, PUM_F32, L.r, EPI_SET, rs);  // b_c = P^T r_f
+  EpiArgs pa{};
+  if (is_mixed(h, l + 1) || l + 1 == (int)h->lv.size() - 1) {
+    const int64_t Nc = (int64_t)C.n * C.d;
+    convert_vec(ctx, C.b64, PUM_F64, C.b, PUM_F32, Nc);
+    vcycle_mixed(ctx, h, l + 1, C.b64, C.z64);
+    pa.y = z;
+    bsr_mv(ctx, L.P, PUM_F64, C.z64, EPI_ADD, pa);  // z += P z_c (FP64)
+  } else {
+    vcycle_level(ctx, h, l + 1);
+    pa.y = z;
+    pa.ydt = PUM_F64;
+    bsr_mv(ctx, L.Ps, PUM_F32, C.x, EPI_ADD, pa);  // z += P x_c
+  }
+  EpiArgs cr{};
+  cr.y = L.c;
+  cr.b = r;
+  cr.xdt = PUM_F64;
+  cr.ydt = PUM_F32;
+  bsr_mv(ctx, L.A, PUM_F32, z, EPI_RESID, cr, tk);     // c = r - A z
+  cheb4(ctx, h, l, L.c, L.e, true, z, PUM_F64, false);  // A e = c from 0; z += updates
+}
+
+static void vcycle_body(pum_ctx* ctx, pum_hier* h, const double* r, double* z) {
+  Level& L0 = h->lv[0];
+  const int64_t N = (int64_t)L0.n * L0.d;
+  if (is_mixed(h, 0) && h->lv.size() > 1) {
+    vcycle_mixed(ctx, h, 0, r, z);
+    return;
+  }
+  convert_vec(ctx, L0.b, h->smooth_dt, r, PUM_F64, N);
+  vcycle_level(ctx, h, 0);
+  convert_vec(ctx, z, PUM_F64, L0.x, h->smooth_dt, N);
+}
+
+static void build_vcycle_graph(pum_ctx* ctx, pum_hier* h, const double* r, double* z) {
   GraphCache& g = h->vgraph;
   graph_destroy(g);
   cudaGraph_t graph = nullptr;
@@ -260,7 +328,7 @@ static void build_vcycle_graph(pum_ctx* ctx, pum_hier* h) {
   PUM_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
   ctx->capture_ev = &g.ev;
   try {
-    vcycle_level(ctx, h, 0);
+    vcycle_body(ctx, h, r, z);
   } catch (...) {
     ctx->capture_ev = nullptr;
     cudaStreamEndCapture(ctx->stream, &graph);
@@ -276,22 +344,22 @@ static void build_vcycle_graph(pum_ctx* ctx, pum_hier* h) {
   cudaGraphDestroy(graph);
   PUM_CUDA(e);
   g.timed = ctx->timing;
+  g.r = r;
+  g.z = z;
 }
 
+// z = B r: replayed from a graph captured for these (r, z) on capturable streams.
 static void vcycle64(pum_ctx* ctx, pum_hier* h, const double* r, double* z) {
-  Level& L0 = h->lv[0];
-  const int64_t N = (int64_t)L0.n * L0.d;
-  convert_vec(ctx, L0.b, h->smooth_dt, r, PUM_F64, N);
-  if (capturable(ctx)) {
-    graph_harvest(ctx, h);
-    if (!h->vgraph.exec || h->vgraph.timed != ctx->timing) build_vcycle_graph(ctx, h);
-    PUM_CUDA(cudaGraphLaunch(h->vgraph.exec, ctx->stream));
-    ctx->launches += h->vgraph.kernels;
-    h->vgraph.pending = h->vgraph.timed;
-  } else {
-    vcycle_level(ctx, h, 0);
+  if (!capturable(ctx)) {
+    vcycle_body(ctx, h, r, z);
+    return;
   }
-  convert_vec(ctx, z, PUM_F64, L0.x, h->smooth_dt, N);
+  graph_harvest(ctx, h);
+  GraphCache& g = h->vgraph;
+  if (!g.exec || g.timed != ctx->timing || g.r != r || g.z != z) build_vcycle_graph(ctx, h, r, z);
+  PUM_CUDA(cudaGraphLaunch(g.exec, ctx->stream));
+  ctx->launches += g.kernels;
+  g.pending = g.timed;
 }
 
 void vcycle_apply_impl(pum_ctx* ctx, pum_hier* h, const double* r, double* z) {

@@ -364,3 +364,32 @@ def test_graph_replay_is_bitwise_identical(lib, small_biharmonic):
     (a1, a2, ax, ah), (b1, b2, bx, bh) = outs
     assert np.array_equal(a1, b1) and np.array_equal(a2, b2) and np.array_equal(a1, a2)
     assert np.array_equal(ax, bx) and ah == bh
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_kernel_timing_counts_every_finest_launch(lib, small_biharmonic, graph):
+    """Per-class event timing works for direct launches and for graph replays."""
+    import torch
+    h = small_biharmonic
+    s = torch.cuda.Stream() if graph else None
+    with torch.cuda.stream(s if graph else torch.cuda.current_stream()):
+        c = lib.Context(0, stream=s.cuda_stream if graph else None)
+        H = hier_from_oracle(lib, c, h)
+        H.setup(p0="lower", adaptive=False, k=PR.cheb_k, smooth="f32", g="f32")
+        x = cuda(np.zeros_like(h.b))
+        c.timing(True)
+        c.timing_reset()
+        rep = H.pcg(cuda(h.b), x, rtol=1e-8, maxit=100, flexible=True)
+        kt = c.timing_read()
+        c.timing(False)
+        torch.cuda.synchronize()
+        H.close()
+        c.close()
+    k, its = PR.cheb_k, rep["iters"] + 1  # one V-cycle before the loop and one per non-final iteration
+    cycles = rep["iters"]
+    # finest level per cycle: k G and k G^T products in each smoother, 2 FP64-operator residuals,
+    # k-1 FP32 residuals in each smoother
+    assert kt["g"][0] == 2 * k * cycles and kt["gt"][0] == 2 * k * cycles
+    assert kt["resid64"][0] == 2 * cycles and kt["resid"][0] == 2 * (k - 1) * cycles
+    assert kt["pcg_ap"][0] == rep["iters"] and all(v[1] > 0 for v in kt.values())
+    del its
