@@ -243,7 +243,10 @@ pum_status pum_hier_destroy(pum_hier *h);
  * Class ids: 0 residual b - A x in the smoother's precision, 1 G r, 2 G^T t + Chebyshev
  * update, 3 A p in PCG, 4 residual with the FP64 operator on FP32 vectors. */
 enum { PUM_TK_RESID = 0, PUM_TK_G = 1, PUM_TK_GT = 2, PUM_TK_PCG_AP = 3, PUM_TK_RESID64 = 4, PUM_TK_COUNT = 5 };
-pum_status pum_timing_enable(pum_ctx *ctx, int enable);
+#define PUM_TIMING_ALL ((1 << PUM_TK_COUNT) - 1)
+/* mask: bit k times class k (PUM_TIMING_ALL: every class; 0: off).  Timing only the classes
+ * of interest keeps the other launches free of event records. */
+pum_status pum_timing_enable(pum_ctx *ctx, int mask);
 pum_status pum_timing_reset(pum_ctx *ctx);
 pum_status pum_timing_read(pum_ctx *ctx, int64_t *launches, double *ms);
 /* Number of kernels of this library launched on the context since creation. */

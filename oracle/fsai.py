@@ -172,6 +172,36 @@ def adaptive_fsai(A: bk.BlockCSR, P0: list[list[int]], t_max: int, tau: float = 
     return AdaptiveResult(final, hist)
 
 
+def adaptive_row(A: bk.BlockCSR, k: int, P0k: list[int], t_max: int, tau: float = 1.0,
+                 tie_rel: float = 1e-9) -> list[int]:
+    """Algorithm 1 for block row k alone.
+
+    The steps of Algorithm 1 only ever change row k's pattern from row k's own scores, so a
+    row's final pattern depends on A near that row only; A needs the rows of P_k, of the
+    admissible columns and of their A-neighbours (a window around k).
+    """
+    Apat = A.pattern()
+    Pk = sorted(P0k)
+    for _t in range(t_max):
+        C = admissible(Apat, Pk, k)
+        if not C:
+            break
+        rhos = row_rhos(A, k, Pk, C)
+        cstar = choose(rhos, tie_rel)
+        if rhos[cstar] < tau:
+            Pk = sorted(Pk + [cstar])
+        else:
+            break
+    return Pk
+
+
+def g_row(A: bk.BlockCSR, k: int, Pk: list[int]) -> dict:
+    """Row k of G = L_S^{-1} F for the pattern row P_k (Definition 2.2)."""
+    row, S = fsai_row(A, k, Pk)
+    J = sla.solve_triangular(np.linalg.cholesky(S), np.eye(A.d), lower=True)
+    return {j: J @ blk for j, blk in row.items()}
+
+
 @dataclasses.dataclass
 class NestedFSAI:
     F0: bk.BlockCSR

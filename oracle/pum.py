@@ -277,14 +277,16 @@ class Assembled:
 
 
 def assemble(m: int, p: int, order: int, gamma, f=None, g=None, q: int | None = None,
-             with_mass: bool = True) -> Assembled:
+             with_mass: bool = True, rows=None) -> Assembled:
     """Stiffness A, load b and mass matrix M of the PUM space of level m.
 
     f(x, y) is the source, g = [g0, g1, (g2)] the boundary data (callables of
     x, y on the boundary), both default to zero.  q = Gauss points per
     direction on each sub-cell (default p + 6, exact for the PU-polynomial
-    integrands of both equations).
+    integrands of both equations).  rows: only these block rows are assembled
+    (the other rows of A, M and b stay empty / zero).
     """
+    keep = None if rows is None else set(int(r) for r in rows)
     eq = Equation(order)
     d = local_dim(p)
     exps = basis_exponents(p)
@@ -318,6 +320,8 @@ def assemble(m: int, p: int, order: int, gamma, f=None, g=None, q: int | None = 
             X, Y = np.meshgrid(px, py, indexing="ij")
             X, Y = np.ravel(X), np.ravel(Y)
             patches = [(ax, ay) for ay in ay_list for ax in ax_list]
+            if keep is not None and not any(pp[1] * m + pp[0] in keep for pp in patches):
+                continue
             vals = {}
             for (ax, ay) in patches:
                 TX, TY = tx.get(ax), ty.get(ay)
@@ -327,6 +331,8 @@ def assemble(m: int, p: int, order: int, gamma, f=None, g=None, q: int | None = 
             fv = f(X, Y) if f is not None else None
             for pi in patches:
                 i = pi[1] * m + pi[0]
+                if keep is not None and i not in keep:
+                    continue
                 psi_i = vals[pi][1]
                 if fv is not None:
                     bvec[i * d:(i + 1) * d] += psi_i @ (W * fv)
@@ -347,6 +353,9 @@ def assemble(m: int, p: int, order: int, gamma, f=None, g=None, q: int | None = 
         fixed = [a for a in range(m) if patch_box_1d(m, a)[0] <= val <= patch_box_1d(m, a)[1]]
         pt = np.array([val])
         for (ps, ws, along_list, tab) in subs:
+            if keep is not None and not any(((ai * m + af) if axis == 0 else (af * m + ai)) in keep
+                                            for ai in along_list for af in fixed):
+                continue
             for af in fixed:
                 Tfix = np.empty((p + 1, rmax + 3, 1))
                 for j in range(p + 1):
@@ -367,6 +376,8 @@ def assemble(m: int, p: int, order: int, gamma, f=None, g=None, q: int | None = 
 
                 for ai in along_list:
                     i = (ai * m + af) if axis == 0 else (af * m + ai)
+                    if keep is not None and i not in keep:
+                        continue
                     if g is not None:
                         xs = np.full_like(ps, val) if axis == 0 else ps
                         ys = ps if axis == 0 else np.full_like(ps, val)
@@ -441,7 +452,7 @@ def local_projection(m: int, p: int, func, q: int = 12) -> np.ndarray:
 # Transfers and Galerkin hierarchy
 # ---------------------------------------------------------------------------
 
-def prolongation(m_f: int, p: int, q: int | None = None) -> bk.BlockCSR:
+def prolongation(m_f: int, p: int, q: int | None = None, rows=None) -> bk.BlockCSR:
     """P: V_{l-1} -> V_l by global-to-local L2 projection (Section 4).
 
     Block (i, j) = M_i^{-1} B_ij with M_i = int_{omega_i cap Omega} theta_i theta_i^T and
@@ -470,11 +481,15 @@ def prolongation(m_f: int, p: int, q: int | None = None) -> bk.BlockCSR:
             out.append((wts, th, co))
         return out
 
-    pcs = [pieces(a) for a in range(m_f)]
+    keep = None if rows is None else set(int(r) for r in rows)
+    need = range(m_f) if keep is None else sorted({r % m_f for r in keep} | {r // m_f for r in keep})
+    pcs = {a: pieces(a) for a in need}
     ent = {}
     for iy in range(m_f):
         for ix in range(m_f):
             i = iy * m_f + ix
+            if keep is not None and i not in keep:
+                continue
             Mi = np.zeros((d, d))
             Bs = {}
             for (wx, thx, cox) in pcs[ix]:

@@ -77,8 +77,16 @@ class Context:
         except Exception:
             pass
 
-    def timing(self, enable: bool):
-        self.check(self.lib.pum_timing_enable(self.h, int(enable)))
+    TK = {"resid": 0, "g": 1, "gt": 2, "pcg_ap": 3, "resid64": 4}
+
+    def timing(self, enable, classes=None):
+        """Enable per-class kernel timing (all classes, or the named ones)."""
+        mask = 0
+        if enable:
+            names = classes or list(self.TK)
+            for n in names:
+                mask |= 1 << self.TK[n]
+        self.check(self.lib.pum_timing_enable(self.h, mask))
 
     def timing_reset(self):
         self.check(self.lib.pum_timing_reset(self.h))

@@ -145,6 +145,9 @@ void finalize_smoother(pum_ctx* ctx, pum_hier* h) {
       }
     }
     if (vdt == PUM_F32) bsr_convert(L.As, L.A, PUM_F32, s);
+    if (vdt == PUM_F32 && L.n >= kSellMinRows && h->sell)
+      for (Bsr* m : {&L.As, &L.G, &L.GT, &L.F0, &L.F0T, &L.G1, &L.G1T, &L.Ps, &L.PTs})
+        if (!m->empty()) sell_build(*m, s);
     for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e}) *v = dalloc(vs * N);
     if (vdt == PUM_F32 && l > 0 && (l < h->sp.mixed_levels || l == nl - 1)) {
       L.b64 = (double*)dalloc(sizeof(double) * N);
@@ -259,6 +262,8 @@ pum_status pum_create(pum_ctx** out, int device, void* cuda_stream) {
     }
     const char* ng = getenv("PUM_NO_GRAPH");
     ctx->graphs = !(ng && ng[0] == '1');
+    const char* ns = getenv("PUM_NO_SELL");
+    ctx->sell = !(ns && ns[0] == '1');
     ctx->status = (DevStatus*)dalloc(sizeof(DevStatus));
     ctx->scal = (double*)dalloc(sizeof(double) * kScalSlots);
     ctx->partials = (double*)dalloc(sizeof(double) * (1 << 16));
@@ -396,6 +401,7 @@ pum_status bfsai_setup(pum_ctx* ctx, pum_hier* h, const bfsai_params* fp, const 
     h->sp = *sp;
     h->smooth_dt = sp->smooth_dt;
     h->g_dt = sp->g_dt;
+    h->sell = ctx->sell;
     const int nl = (int)h->lv.size();
     PUM_CHECK(h->lv.back().n * h->lv.back().d <= 4096, PUM_ERR_UNSUPPORTED, "coarsest level above 4096 unknowns");
     for (int l = 0; l + 1 < nl; ++l) {
@@ -652,6 +658,7 @@ pum_status pum_hier_load(pum_ctx* ctx, const char* path, pum_hier** out) {
       check_params(&h->fp, &h->sp);
       h->smooth_dt = h->sp.smooth_dt;
       h->g_dt = h->sp.g_dt;
+      h->sell = ctx->sell;
       int32_t nl;
       rd(f, &nl, sizeof(nl));
       PUM_CHECK(nl >= 1 && nl <= 16, PUM_ERR_IO, "corrupt level count");
@@ -701,9 +708,9 @@ pum_status pum_hier_destroy(pum_hier* h) {
   return PUM_OK;
 }
 
-pum_status pum_timing_enable(pum_ctx* ctx, int enable) {
-  if (!ctx) return PUM_ERR_INVALID_ARG;
-  ctx->timing = enable != 0;
+pum_status pum_timing_enable(pum_ctx* ctx, int mask) {
+  if (!ctx || mask < 0 || mask >= (1 << PUM_TK_COUNT)) return PUM_ERR_INVALID_ARG;
+  ctx->timing = mask;
   return PUM_OK;
 }
 

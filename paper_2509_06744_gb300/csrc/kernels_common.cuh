@@ -1,0 +1,73 @@
+// Device helpers shared by the BSR and sliced-block product kernels: accumulation types,
+// vectorised row loads and the fused epilogues (residual, Chebyshev-4 updates of Algorithm 3).
+#pragma once
+
+#include "pum_internal.cuh"
+
+namespace pum {
+
+template <typename T> struct AccOf { using type = float; };
+template <> struct AccOf<double> { using type = double; };
+
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ double to_f(double v) { return v; }
+
+// Load the D contiguous values starting at p (alignment known from D and the layout)
+// into registers, converting to the accumulation type.
+template <int D, typename T, typename AT>
+__device__ __forceinline__ void load_row(const T* __restrict__ p, AT (&out)[D]) {
+  if constexpr (sizeof(T) == 4 && (D % 2) == 0) {
+    const float2* q = reinterpret_cast<const float2*>(p);
+#pragma unroll
+    for (int i = 0; i < D / 2; ++i) {
+      float2 v = __ldg(q + i);
+      out[2 * i] = (AT)v.x;
+      out[2 * i + 1] = (AT)v.y;
+    }
+  } else if constexpr (sizeof(T) == 8 && (D % 2) == 0) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int i = 0; i < D / 2; ++i) {
+      double2 v = __ldg(q + i);
+      out[2 * i] = (AT)v.x;
+      out[2 * i + 1] = (AT)v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < D; ++i) out[i] = (AT)to_f(p[i]);
+  }
+}
+
+// Epilogue of the product acc = (M x)_tid for output unknown tid.
+template <int EPI, typename AT, typename XT, typename YT, typename X2T>
+__device__ __forceinline__ void epilogue(const EpiArgs& e, int64_t tid, AT acc) {
+  YT* y = (YT*)e.y;
+  X2T* x2 = (X2T*)e.xo2;
+  if constexpr (EPI == EPI_SET) {
+    y[tid] = (YT)acc;
+  } else if constexpr (EPI == EPI_RESID) {
+    // b - A x, formed in the accumulation precision (FP64 for an FP64 operator)
+    y[tid] = (YT)((AT)((const XT*)e.b)[tid] - acc);
+  } else if constexpr (EPI == EPI_ADD) {
+    y[tid] = (YT)((AT)y[tid] + acc);
+  } else if constexpr (EPI == EPI_CHEB_FIRST0) {
+    YT* xo = (YT*)e.xo;
+    y[tid] = (YT)acc;
+    xo[tid] = (YT)((AT)e.dmu * acc);
+    if (x2) x2[tid] = e.x2_set ? (X2T)(e.dmu * (double)acc) : (X2T)((double)x2[tid] + e.dmu * (double)acc);
+  } else if constexpr (EPI == EPI_CHEB_FIRST) {
+    YT* xo = (YT*)e.xo;
+    y[tid] = (YT)acc;
+    xo[tid] = (YT)((AT)xo[tid] + (AT)e.dmu * acc);
+    if (x2) x2[tid] = (X2T)((double)x2[tid] + e.dmu * (double)acc);
+  } else if constexpr (EPI == EPI_CHEB) {
+    YT* xo = (YT*)e.xo;
+    const AT pn = (AT)e.mu2 * (AT)y[tid] + acc;
+    y[tid] = (YT)pn;
+    xo[tid] = (YT)((AT)xo[tid] + (AT)e.dmu * pn);
+    if (x2) x2[tid] = (X2T)((double)x2[tid] + e.dmu * (double)pn);
+  }
+}
+
+}  // namespace pum

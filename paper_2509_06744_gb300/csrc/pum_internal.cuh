@@ -63,7 +63,21 @@ inline int block_stride(int d, int dt) {
   return (d * d + per16 - 1) / per16 * per16;
 }
 
+// Sliced block copy of a BSR matrix used by the smoother's products on large levels:
+// block rows in groups of R, group g padded to S_g slots (its longest row); the values of
+// (slot, block column c) are contiguous over the group's R*d output unknowns.
+struct Sell {
+  int R = 0;            // block rows per group (0: not built)
+  int n_groups = 0;
+  int64_t slots = 0;    // total slots
+  int max_slots = 0;    // longest group
+  int* goff = nullptr;  // n_groups + 1 slot offsets
+  int* cols = nullptr;  // slots * R block columns, -1 for padding
+  void* vals = nullptr; // slots * d * R * d values
+};
+
 struct Bsr {
+  Sell sell;
   int n_brows = 0, n_bcols = 0, d = 0, stride = 0, dt = PUM_F64;
   int max_row_nnzb = 0;  // longest block row
   int64_t nnzb = 0;
@@ -75,6 +89,12 @@ struct Bsr {
 };
 
 void bsr_free(Bsr& m);
+// Sliced layout (sell.cu): build for a FP32/BF16 matrix; product through it (false: not applicable).
+void sell_build(Bsr& m, cudaStream_t s);
+void sell_free(Sell& s);
+bool sell_mv(pum_ctx* ctx, const Bsr& M, int vdt, const void* x, int epi, const struct EpiArgs& e);
+constexpr int kSellMinRows = 32768;  // levels with at least this many block rows use it (one thread
+                                      // per output then fills the GPU)
 // Allocate a device BSR with the given host pattern (values uninitialised).
 void bsr_alloc(Bsr& m, int n_brows, int n_bcols, int d, int dt, const std::vector<int>& rp,
                const std::vector<int>& ci);
@@ -131,7 +151,7 @@ struct TimedEvent {
 struct GraphCache {
   cudaGraphExec_t exec = nullptr;
   int64_t kernels = 0;  // kernel launches per replay
-  bool timed = false;
+  int timed = 0;  // timing mask the graph was captured with
   bool pending = false;  // a timed replay whose events have not been collected
   std::vector<TimedEvent> ev;
   const double* r = nullptr;  // vectors the graph was captured for
@@ -153,6 +173,7 @@ struct pum_hier {
   // FP64 work vectors of the finest level (PCG, conversions)
   double* w64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   pum::GraphCache vgraph;  // captured V-cycle
+  bool sell = true;        // sliced layouts for the large levels' FP32 products
 };
 
 struct pum_ctx {
@@ -166,7 +187,7 @@ struct pum_ctx {
   double* h_scal = nullptr;          // pinned host mirror of scal
   int64_t launches = 0;
   int sm_count = 152;
-  bool timing = false;
+  int timing = 0;  // bitmask of timed kernel classes (1 << PUM_TK_*)
   cudaEvent_t ev_pool[2][PUM_TK_COUNT];
   std::vector<cudaEvent_t> tk_start[PUM_TK_COUNT], tk_stop[PUM_TK_COUNT];
   int64_t tk_launches[PUM_TK_COUNT] = {};  // launches timed since the last reset (collected)
@@ -174,6 +195,7 @@ struct pum_ctx {
   int64_t tk_pool_used[PUM_TK_COUNT] = {}; // event pairs of direct launches not yet collected
   std::vector<pum::TimedEvent>* capture_ev = nullptr;  // set while a graph is being captured
   bool graphs = true;                                   // capture the V-cycle when the stream allows it
+  bool sell = true;                                     // sliced layouts on large levels
 };
 
 namespace pum {

@@ -10,7 +10,7 @@ namespace pum {
 // ----------------------------------------------------------------------------- timing
 
 void timing_begin(pum_ctx* ctx, int tk) {
-  if (!ctx->timing) return;
+  if (!((ctx->timing >> tk) & 1)) return;
   if (ctx->capture_ev) {  // inside a graph capture: the graph gets its own event pair
     TimedEvent t{tk, nullptr, nullptr};
     PUM_CUDA(cudaEventCreate(&t.start));
@@ -31,7 +31,7 @@ void timing_begin(pum_ctx* ctx, int tk) {
 }
 
 void timing_end(pum_ctx* ctx, int tk) {
-  if (!ctx->timing) return;
+  if (!((ctx->timing >> tk) & 1)) return;
   if (ctx->capture_ev) {
     PUM_CUDA(cudaEventRecordWithFlags(ctx->capture_ev->back().stop, ctx->stream, cudaEventRecordExternal));
     return;
@@ -359,7 +359,7 @@ static void vcycle64(pum_ctx* ctx, pum_hier* h, const double* r, double* z) {
   if (!g.exec || g.timed != ctx->timing || g.r != r || g.z != z) build_vcycle_graph(ctx, h, r, z);
   PUM_CUDA(cudaGraphLaunch(g.exec, ctx->stream));
   ctx->launches += g.kernels;
-  g.pending = g.timed;
+  g.pending = g.timed != 0;
 }
 
 void vcycle_apply_impl(pum_ctx* ctx, pum_hier* h, const double* r, double* z) {

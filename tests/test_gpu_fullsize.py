@@ -1,0 +1,144 @@
+"""GPU parity at the benchmark size (256x256 patches, 655,360 unknowns, 9 levels).
+
+The oracle cannot build the whole problem in seconds, so it computes sampled outputs one
+by one: block rows of A, b and P assembled alone (corners, edges, interior), Galerkin rows
+of the first coarse level from the fine rows they need, and Algorithm 1 for single rows
+from a window of A around them.  Properties that hold at any size (V-cycle symmetry, PCG
+convergence, FP32 form against FP64 form) cover the solve.
+"""
+import numpy as np
+import pytest
+
+import pum_inputs as pin
+from oracle import fsai, pum
+from _util import TOL_ASSEMBLY, TOL_FSAI, cuda, from_export, host
+
+pytestmark = pytest.mark.gpu
+
+PR = pin.BIHARMONIC_256
+M = PR.finest_m
+SAMPLE = [0, 255, 65280, 65535, 128, 32768, 33023, 128 * 256 + 128, 1000, 50000]
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    import paper_2509_06744_gb300 as L
+    ctx = L.Context(0)
+    b = torch.zeros(PR.n_dofs, dtype=torch.float64, device="cuda")
+    H = L.Hierarchy.assemble(ctx, PR.equation, PR.p, M, PR.n_levels, f_coef=pin.fourier_coefficients(PR.rhs_seed),
+                             f_decay=PR.rhs_decay, nitsche=PR.nitsche, b=b)
+    yield L, ctx, H, b
+    H.close()
+    ctx.close()
+
+
+@pytest.fixture(scope="module")
+def exported(gpu):
+    L, ctx, H, b = gpu
+    return {"A0": from_export(H.export(0, L.PUM_MAT_A)), "P0": from_export(H.export(0, L.PUM_MAT_P)),
+            "A1": from_export(H.export(1, L.PUM_MAT_A)), "b": host(b)}
+
+
+def _oracle_rows(rows):
+    f = pum.fourier_source(pin.fourier_coefficients(PR.rhs_seed), PR.rhs_decay)
+    g = pum.nitsche_gamma(PR.equation, PR.p, M, PR.nitsche)
+    return pum.assemble(M, PR.p, PR.equation, g, f=f, with_mass=False, rows=rows)
+
+
+def _window(k, radius, m=M):
+    kx, ky = k % m, k // m
+    return [iy * m + ix for iy in range(max(ky - radius, 0), min(ky + radius + 1, m))
+            for ix in range(max(kx - radius, 0), min(kx + radius + 1, m))]
+
+
+def test_assembled_rows_match_oracle(exported):
+    asm = _oracle_rows(SAMPLE)
+    A, b = exported["A0"], exported["b"]
+    scale = np.max(np.abs(A.blocks))
+    for k in SAMPLE:
+        assert list(A.row(k)) == list(asm.A.row(k)), f"pattern of row {k}"
+        for j in A.row(k):
+            assert np.max(np.abs(A.block(k, j) - asm.A.block(k, j))) <= TOL_ASSEMBLY * scale
+        d = PR.d
+        assert np.max(np.abs(b[k * d:(k + 1) * d] - asm.b[k * d:(k + 1) * d])) <= TOL_ASSEMBLY * np.max(np.abs(b))
+    assert A.nnzb == (3 * M - 2) ** 2
+
+
+def test_prolongation_rows_match_oracle(exported):
+    P = exported["P0"]
+    ref = pum.prolongation(M, PR.p, rows=SAMPLE)
+    for k in SAMPLE:
+        assert list(P.row(k)) == list(ref.row(k))
+        for j in P.row(k):
+            assert np.max(np.abs(P.block(k, j) - ref.block(k, j))) <= TOL_ASSEMBLY * np.max(np.abs(ref.block(k, j)))
+
+
+def test_galerkin_rows_of_first_coarse_level(exported):
+    """A_1 = P^T A_0 P row by row from the oracle's own fine rows."""
+    mc = M // 2
+    P_gpu_pattern = exported["P0"]
+    for bc in [0, mc * (mc // 2) + mc // 2, mc * mc - 1, 5 * mc + 3]:
+        bx, by = bc % mc, bc // mc
+        fine = [iy * M + ix for iy in range(max(2 * by - 1, 0), min(2 * by + 3, M))
+                for ix in range(max(2 * bx - 1, 0), min(2 * bx + 3, M))]
+        halo = sorted({j for a in fine for j in _window(a, 1)})
+        asm = _oracle_rows(fine)
+        P = pum.prolongation(M, PR.p, rows=halo)
+        row = {}
+        for a in fine:
+            Pab = P.block(a, bc)
+            if Pab is None:
+                continue
+            for a2 in asm.A.row(a):
+                Aaa = asm.A.block(a, a2)
+                for c in P.row(a2):
+                    row[c] = row.get(c, 0.0) + Pab.T @ Aaa @ P.block(a2, c)
+        A1 = exported["A1"]
+        assert sorted(row) == list(A1.row(bc))
+        scale = max(np.max(np.abs(v)) for v in row.values())
+        for c, v in row.items():
+            assert np.max(np.abs(A1.block(bc, c) - v)) <= 1e-11 * scale
+    del P_gpu_pattern
+
+
+def test_adaptive_fsai_rows_at_full_size(gpu, exported):
+    """Algorithm 1 (P0 = lower(P(A)), t_max = 6, tau = 1): sampled rows bit-exact in pattern."""
+    L, ctx, H, b = gpu
+    H.setup(p0="lower", adaptive=True, t_max=PR.t_max, tau=PR.tau, k=PR.cheb_k)
+    G = from_export(H.export(0, L.PUM_MAT_G))
+    for k in [0, 257, 128 * 256 + 128, 65535, 40000]:
+        win = _window(k, 8)
+        A = _oracle_rows(win).A
+        P0k = [c for c in A.row(k) if c <= k]
+        Pk = fsai.adaptive_row(A, k, P0k, PR.t_max, PR.tau)
+        assert list(G.row(k)) == Pk, f"adaptive pattern of row {k}"
+        ref = fsai.g_row(A, k, Pk)
+        scale = max(np.max(np.abs(v)) for v in ref.values())
+        for j, v in ref.items():
+            assert np.max(np.abs(G.block(k, j) - v)) <= TOL_FSAI * scale
+
+
+def test_vcycle_symmetric_and_pcg_forms_agree(gpu):
+    """At full size: the FP64 cycle is symmetric; FP64 and FP32 forms reach 1e-8 with equal solutions."""
+    import torch
+    L, ctx, H, b = gpu
+    H.setup(p0="lower", adaptive=True, t_max=PR.t_max, tau=PR.tau, k=PR.cheb_k)
+    u = cuda(pin.normal_vector(PR.n_dofs, 1))
+    v = cuda(pin.normal_vector(PR.n_dofs, 2))
+    Bu, Bv = torch.zeros_like(u), torch.zeros_like(u)
+    H.vcycle(u, Bu)
+    H.vcycle(v, Bv)
+    lhs, rhs = float(Bu @ v), float(u @ Bv)
+    assert abs(lhs - rhs) <= 1e-10 * float(torch.linalg.norm(Bu) * torch.linalg.norm(v))
+    x64 = torch.zeros_like(b)
+    rep64 = H.pcg(b, x64, rtol=1e-8, maxit=100)
+    H.setup(p0="lower", adaptive=True, t_max=PR.t_max, tau=PR.tau, k=PR.cheb_k, smooth="f32", g="f32")
+    x32 = torch.zeros_like(b)
+    rep32 = H.pcg(b, x32, rtol=1e-8, maxit=100, flexible=True)
+    assert rep64["converged"] and rep32["converged"]
+    assert rep32["iters"] <= rep64["iters"] + 1
+    assert float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64)) <= 1e-7
+    r = torch.zeros_like(b)
+    H.residual(0, b, x32, r)
+    assert float(torch.linalg.norm(r) / torch.linalg.norm(b)) <= 1e-5  # FP64 rounding floor of A x here

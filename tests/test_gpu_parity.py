@@ -312,6 +312,38 @@ def test_block_sizes_residual_and_static_fsai(lib, ctx, d):
     assert max_rel(G.blocks, ref.G.blocks) <= TOL_FSAI
 
 
+@pytest.mark.parametrize("d", [6, 10, 21])
+def test_sliced_layout_products_on_large_levels(lib, d):
+    """Levels with >= 32768 block rows smooth through the sliced block layout: same results as
+    the block-row kernel (FP32 rounding) and as the FP64 Algorithm 3 of the oracle."""
+    import os
+    import torch
+    side = 182  # 33,124 block rows
+    A = _random_block_spd(side, d, seed=3 + d)
+    P = bk.from_blocks(A.n_rows, 1, d, {(i, 0): np.eye(d) for i in range(A.n_rows)})
+    N = A.n_rows * d
+    b = pin.normal_vector(N, 11)
+    outs = {}
+    for sell in (True, False):
+        if not sell:
+            os.environ["PUM_NO_SELL"] = "1"
+        try:
+            c = lib.Context(0)
+        finally:
+            os.environ.pop("PUM_NO_SELL", None)
+        H = lib.Hierarchy.from_bsr(c, [to_view(A), None], [to_pview(P)])
+        H.setup(p0="diag", k=3, smooth="f32", g="f32", mixed_levels=0)
+        x = cuda(np.zeros(N))
+        H.cheb4_smooth(0, cuda(b), x, True)
+        outs[sell] = (host(x), H.info(0)["beta"])
+        H.close()
+        c.close()
+    assert norm_rel(outs[True][0], outs[False][0]) <= 1e-5
+    ref = fsai.fsai(A, fsai.diag_pattern(A.n_rows))  # block Jacobi (Remark 2.4): cheap at this size
+    xr = cheb.cheb4(A.matvec, lambda r: fsai.apply_M(ref.G, r), b, None, outs[True][1], 3)
+    assert norm_rel(outs[True][0], xr) <= 1e-5
+
+
 def test_invalid_arguments_are_reported(lib, ctx, static_pair):
     import torch
     H, _ = static_pair
@@ -368,7 +400,7 @@ def test_graph_replay_is_bitwise_identical(lib, small_biharmonic):
 
 @pytest.mark.parametrize("graph", [False, True])
 def test_kernel_timing_counts_every_finest_launch(lib, small_biharmonic, graph):
-    """Per-class event timing works for direct launches and for graph replays."""
+    """Per-class event timing works for direct launches and for graph replays, per class."""
     import torch
     h = small_biharmonic
     s = torch.cuda.Stream() if graph else None
@@ -381,15 +413,19 @@ def test_kernel_timing_counts_every_finest_launch(lib, small_biharmonic, graph):
         c.timing_reset()
         rep = H.pcg(cuda(h.b), x, rtol=1e-8, maxit=100, flexible=True)
         kt = c.timing_read()
+        c.timing(True, ["gt"])
+        c.timing_reset()
+        H.pcg(cuda(h.b), x, rtol=1e-8, maxit=100, flexible=True)
+        kt_gt = c.timing_read()
         c.timing(False)
         torch.cuda.synchronize()
         H.close()
         c.close()
-    k, its = PR.cheb_k, rep["iters"] + 1  # one V-cycle before the loop and one per non-final iteration
-    cycles = rep["iters"]
+    k, cycles = PR.cheb_k, rep["iters"]  # one V-cycle before the loop and one per non-final iteration
     # finest level per cycle: k G and k G^T products in each smoother, 2 FP64-operator residuals,
     # k-1 FP32 residuals in each smoother
     assert kt["g"][0] == 2 * k * cycles and kt["gt"][0] == 2 * k * cycles
     assert kt["resid64"][0] == 2 * cycles and kt["resid"][0] == 2 * (k - 1) * cycles
     assert kt["pcg_ap"][0] == rep["iters"] and all(v[1] > 0 for v in kt.values())
-    del its
+    # with only the G^T class selected, the other classes record nothing
+    assert kt_gt["gt"][0] == kt["gt"][0] and all(kt_gt[n][0] == 0 for n in ("resid", "g", "pcg_ap", "resid64"))
