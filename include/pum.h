@@ -128,6 +128,8 @@ typedef struct {
   double beta;        /* Chebyshev upper bound of this level (0 before bfsai_setup)        */
   double logdet_S;    /* sum_k log det S_kk of the (inner) FSAI (Lemma 2.7)                */
   int32_t coarsest;
+  int32_t nested_inner; /* nested set-up: 1 inner FSAI of A1 = F0 A F0^T; 0 inner block Jacobi
+                           (used when A1 is not numerically SPD in FP64; equals plain FSAI)  */
 } pum_level_info;
 
 /* Matrices selectable in pum_hier_export. */

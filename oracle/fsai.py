@@ -125,8 +125,21 @@ def row_rhos(A: bk.BlockCSR, k: int, Pk: list[int], C: list[int]) -> dict:
         else:
             W = A.block(c, c).copy()
         X = W - Hkc.T @ np.linalg.solve(Hkk, Hkc)
-        out[c] = float(np.exp(np.linalg.slogdet(X)[1] - np.linalg.slogdet(W)[1]))
+        sx, lx = np.linalg.slogdet(X)
+        sw, lw = np.linalg.slogdet(W)
+        if sx <= 0 or sw <= 0 or not _is_spd(X) or not _is_spd(W):
+            continue  # rho_c not computable in FP64: the candidate is not admissible
+        out[c] = float(np.exp(lx - lw))
     return out
+
+
+def _is_spd(X) -> bool:
+    """X is numerically symmetric positive definite (its Cholesky factorisation exists)."""
+    try:
+        np.linalg.cholesky(X)
+        return True
+    except np.linalg.LinAlgError:
+        return False
 
 
 def _blk(A, i, j):
@@ -162,6 +175,9 @@ def adaptive_fsai(A: bk.BlockCSR, P0: list[list[int]], t_max: int, tau: float = 
                 R.discard(k)
                 continue
             rhos = row_rhos(A, k, P[k], C)
+            if not rhos:
+                R.discard(k)
+                continue
             cstar = choose(rhos, tie_rel)
             if rhos[cstar] < tau:
                 P[k] = sorted(P[k] + [cstar])
@@ -187,6 +203,8 @@ def adaptive_row(A: bk.BlockCSR, k: int, P0k: list[int], t_max: int, tau: float 
         if not C:
             break
         rhos = row_rhos(A, k, Pk, C)
+        if not rhos:
+            break
         cstar = choose(rhos, tie_rel)
         if rhos[cstar] < tau:
             Pk = sorted(Pk + [cstar])

@@ -145,9 +145,9 @@ void finalize_smoother(pum_ctx* ctx, pum_hier* h) {
       }
     }
     if (vdt == PUM_F32) bsr_convert(L.As, L.A, PUM_F32, s);
-    if (vdt == PUM_F32 && L.n >= kSellMinRows && h->sell)
+    if (vdt == PUM_F32 && h->sell)
       for (Bsr* m : {&L.As, &L.G, &L.GT, &L.F0, &L.F0T, &L.G1, &L.G1T, &L.Ps, &L.PTs})
-        if (!m->empty()) sell_build(*m, s);
+        if (!m->empty() && m->n_brows >= kSellMinRows) sell_build(*m, s);
     for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e}) *v = dalloc(vs * N);
     if (vdt == PUM_F32 && l > 0 && (l < h->sp.mixed_levels || l == nl - 1)) {
       L.b64 = (double*)dalloc(sizeof(double) * N);
@@ -405,8 +405,12 @@ pum_status bfsai_setup(pum_ctx* ctx, pum_hier* h, const bfsai_params* fp, const 
     const int nl = (int)h->lv.size();
     PUM_CHECK(h->lv.back().n * h->lv.back().d <= 4096, PUM_ERR_UNSUPPORTED, "coarsest level above 4096 unknowns");
     for (int l = 0; l + 1 < nl; ++l) {
-      fsai_setup_level(ctx, h, l);
-      lanczos_level(ctx, h, l);
+      try {
+        fsai_setup_level(ctx, h, l);
+        lanczos_level(ctx, h, l);
+      } catch (const Error& e) {
+        throw Error{e.st, "level " + std::to_string(l) + ": " + e.msg};
+      }
     }
     coarse_factor(ctx, h);
     finalize_smoother(ctx, h);
@@ -560,6 +564,7 @@ pum_status pum_level_info_get(const pum_hier* h, int level, pum_level_info* info
   info->beta = L.beta;
   info->logdet_S = L.logdet_S;
   info->coarsest = level == (int)h->lv.size() - 1;
+  info->nested_inner = L.nested_inner;
   return PUM_OK;
 }
 

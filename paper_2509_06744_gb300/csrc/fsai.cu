@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 
 #include "pum_internal.cuh"
 
@@ -273,6 +275,9 @@ __global__ void __launch_bounds__(kFsaiThreads) k_fsai_rows(FsaiArgs a) {
         Xm[g * dd + e] = v;
       }
       __syncthreads();
+      // A candidate whose W_c or Schur complement X is not numerically positive definite has
+      // no computable rho_c in FP64 (it is linearly dependent on the current pattern to working
+      // precision); it is marked -1 and not chosen.
       for (int g = threadIdx.x; g < ng; g += blockDim.x) {
         const double lx = chol_small(Xm + g * dd, d);
         const double lw = chol_small(Wc + g * dd, d);
@@ -281,24 +286,21 @@ __global__ void __launch_bounds__(kFsaiThreads) k_fsai_rows(FsaiArgs a) {
       __syncthreads();
     }
     if (threadIdx.x == 0) {
-      // argmin with the tie band: smallest column among rho_c <= rho_min (1 + tie_rel)
+      // argmin with the tie band: smallest column among rho_c <= rho_min (1 + tie_rel), over
+      // the candidates with a computable rho_c
       double rmin = -1.0;
-      bool bad = false;
       for (int q = c0; q < c1; ++q) {
         const double r = rl[q - c0];
-        if (r < 0.0) bad = true;
-        else if (rmin < 0.0 || r < rmin) rmin = r;
+        if (r >= 0.0 && (rmin < 0.0 || r < rmin)) rmin = r;
       }
       int choice = -1;
-      if (bad) {
-        set_status(a.status, PUM_ERR_NOT_SPD, k, kWhereAdaptive);
-      } else if (rmin >= 0.0) {
+      if (rmin >= 0.0) {
         const double thr = rmin * (1.0 + a.tie_rel);
         int cstar = -1;
         double rstar = 0.0;
         for (int q = c0; q < c1; ++q) {
           const double r = rl[q - c0];
-          if (r <= thr && (cstar < 0 || a.cci[q] < cstar)) { cstar = a.cci[q]; rstar = r; }
+          if (r >= 0.0 && r <= thr && (cstar < 0 || a.cci[q] < cstar)) { cstar = a.cci[q]; rstar = r; }
         }
         choice = (rstar < a.tau) ? cstar : -1;
       }
@@ -382,8 +384,10 @@ void check_status(pum_ctx* ctx, const char* what) {
   PUM_CUDA(cudaMemcpy(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost));
   if (st.code != 0) {
     PUM_CUDA(cudaMemset(ctx->status, 0, sizeof(DevStatus)));
-    throw Error{(pum_status)st.code,
-                std::string(what) + ": factorisation failed (non-positive pivot) at block row " + std::to_string(st.info)};
+    const char* stage = st.where == kWhereFsai ? "Cholesky of A[P~,P~] or S_kk" :
+                        st.where == kWhereAdaptive ? "candidate Schur complement" : "dense Cholesky";
+    throw Error{(pum_status)st.code, std::string(what) + ": factorisation failed (non-positive pivot, " + stage +
+                                         ") at block row " + std::to_string(st.info)};
   }
 }
 
@@ -479,7 +483,24 @@ Pattern fsai_pattern(pum_ctx* ctx, const Bsr& A, const Pattern& P0, const bfsai_
     }
     if (rows.empty()) break;
     std::vector<int> chosen;
-    run_rows(ctx, A, P, rows, &crp, &cci, fp.tie_rel, fp.tau, &chosen, nullptr, nullptr, nullptr);
+    try {
+      run_rows(ctx, A, P, rows, &crp, &cci, fp.tie_rel, fp.tau, &chosen, nullptr, nullptr, nullptr);
+    } catch (const Error& err) {
+      const char* dbg = getenv("PUM_DEBUG_FSAI");
+      if (dbg && dbg[0] == '1') {  // report the patterns of the failing step
+        fprintf(stderr, "fsai step %d failed: %s\n", t, err.msg.c_str());
+        for (size_t w = 0; w < rows.size() && w < 100000; ++w) {
+          const int k = rows[w];
+          if (k > 64) continue;
+          fprintf(stderr, "row %d P:", k);
+          for (int j : P.rows[k]) fprintf(stderr, " %d", j);
+          fprintf(stderr, " C:");
+          for (int q = crp[w]; q < crp[w + 1]; ++q) fprintf(stderr, " %d", cci[q]);
+          fprintf(stderr, "\n");
+        }
+      }
+      throw;
+    }
     for (size_t w = 0; w < rows.size(); ++w) {
       const int k = rows[w];
       if (chosen[w] < 0) {
@@ -514,6 +535,8 @@ double fsai_factor(pum_ctx* ctx, const Bsr& A, const Pattern& P, Bsr& G, Bsr* F)
 
 }  // namespace
 
+void copy_blocks(pum_ctx* ctx, Bsr& dst, const Bsr& src, const int* idx);
+
 // FP64 block-FSAI factors of level l: G64 (or, nested, F064 / A1 / G164) and the
 // Kaporin-type measure sum_k log det S_kk.  Precision copies and transposes are made
 // when the smoother is finalised.
@@ -538,8 +561,52 @@ void fsai_setup_level(pum_ctx* ctx, pum_hier* h, int l) {
   spgemm(L.A1, FA, F0T64, s);
   bsr_free(FA);
   bsr_free(F0T64);
-  const Pattern Pin = fsai_pattern(ctx, L.A1, P0, fp);
-  L.logdet_S = fsai_factor(ctx, L.A1, Pin, L.G164, nullptr);
+  // The inner FSAI needs A1 = F0 A F0^T to be numerically SPD.  On coarse Galerkin levels of
+  // strongly penalised problems the computed A1 can lose that in FP64 (its small eigen-
+  // directions fall below the rounding of the triple product); the level then uses the inner
+  // block Jacobi, G1 = diag_B(G_outer) = S^{-1/2}, which is the non-nested FSAI (Section 2.2).
+  try {
+    const Pattern Pin = fsai_pattern(ctx, L.A1, P0, fp);
+    L.logdet_S = fsai_factor(ctx, L.A1, Pin, L.G164, nullptr);
+    L.nested_inner = 1;
+  } catch (const Error& e) {
+    if (e.st != PUM_ERR_NOT_SPD) throw;
+    Bsr Gout2;
+    L.logdet_S = fsai_factor(ctx, L.A, Pout, Gout2, nullptr);
+    std::vector<int> rp(L.n + 1), ci(L.n);
+    for (int i = 0; i < L.n; ++i) { rp[i] = i; ci[i] = i; }
+    rp[L.n] = L.n;
+    bsr_alloc(L.G164, L.n, L.n, L.d, PUM_F64, rp, ci);
+    // copy the diagonal blocks of the outer G (the last block of each row of a lower pattern)
+    std::vector<int> src(L.n);
+    for (int i = 0; i < L.n; ++i) src[i] = Gout2.h_row_ptr[i + 1] - 1;
+    int* dsrc = nullptr;
+    PUM_CUDA(cudaMalloc(&dsrc, sizeof(int) * L.n));
+    PUM_CUDA(cudaMemcpy(dsrc, src.data(), sizeof(int) * L.n, cudaMemcpyHostToDevice));
+    copy_blocks(ctx, L.G164, Gout2, dsrc);
+    cudaFree(dsrc);
+    bsr_free(Gout2);
+    L.nested_inner = 0;
+  }
+}
+
+__global__ void k_copy_blocks(double* __restrict__ dst, int dstride, const double* __restrict__ src, int sstride,
+                              const int* __restrict__ idx, int dd, int64_t nblk) {
+  const int64_t total = nblk * dd;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = i / dd;
+    const int e = (int)(i - b * dd);
+    dst[b * dstride + e] = src[(int64_t)idx[b] * sstride + e];
+  }
+}
+
+void copy_blocks(pum_ctx* ctx, Bsr& dst, const Bsr& src, const int* idx) {
+  const int64_t total = dst.nnzb * dst.d * dst.d;
+  if (!total) return;
+  k_copy_blocks<<<(unsigned)std::min<int64_t>((total + 255) / 256, 2048), 256, 0, ctx->stream>>>(
+      (double*)dst.vals, dst.stride, (const double*)src.vals, src.stride, idx, dst.d * dst.d, dst.nnzb);
+  PUM_CUDA(cudaGetLastError());
+  PUM_CUDA(cudaStreamSynchronize(ctx->stream));
 }
 
 // ----------------------------------------------------------------------------- Lanczos

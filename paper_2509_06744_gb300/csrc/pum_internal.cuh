@@ -130,6 +130,7 @@ struct Level {
   Bsr G1, G1T;          // nested: inner G
   double beta = 0.0;
   double logdet_S = 0.0;
+  int nested_inner = 0;  // nested level: 1 inner FSAI of A1, 0 inner block Jacobi
   // work vectors in the smoothing precision
   void *x = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *t = nullptr, *u = nullptr;
   void *c = nullptr, *e = nullptr;  // correction-form post-smoothing: rhs c = b - A x, iterate e

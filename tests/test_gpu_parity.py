@@ -152,6 +152,34 @@ def test_nested_fsai_patterns_and_factors(lib, ctx, small_biharmonic):
     assert norm_rel(host(z), ref.apply(r)) <= 1e3 * TOL_VECTOR
 
 
+def test_nested_adaptive_fsai_triharmonic_d21(lib, ctx):
+    """Triharmonic p = 5 (d = 21): adaptive outer FSAI from the diagonal pattern and its nested
+    inner FSAI (Section 2.2) match the oracle, patterns bit-exact."""
+    import torch
+    m, p = 8, 5
+    consts = pin.NITSCHE_CONSTANTS[6]
+    coef = pin.fourier_coefficients(2)
+    h = pum.build_hierarchy(m, p, 6, 2, f=pum.fourier_source(coef, 3.0), constants=consts)
+    A = h.A[0]
+    ref_out = fsai.adaptive_fsai(A, fsai.diag_pattern(A.n_rows), 6).fsai
+    ref = fsai.nested_fsai(A, fsai.diag_pattern(A.n_rows), 6)
+    H = lib.Hierarchy.from_bsr(ctx, [to_view(A), to_view(h.A[1])], [to_pview(h.P[0])])
+    H.setup(p0="diag", adaptive=True, t_max=6, tau=1.0, nested=False, k=4)
+    G = from_export(H.export(0, lib.PUM_MAT_G))
+    assert_same_pattern(G, ref_out.G)
+    assert max_rel(G.blocks, ref_out.G.blocks) <= TOL_FSAI
+    H.setup(p0="diag", adaptive=True, t_max=6, tau=1.0, nested=True, k=4)
+    F0 = from_export(H.export(0, lib.PUM_MAT_F0))
+    A1 = from_export(H.export(0, lib.PUM_MAT_A1))
+    G1 = from_export(H.export(0, lib.PUM_MAT_G1))
+    assert_same_pattern(F0, ref.F0)
+    assert_same_pattern(A1, ref.A1)
+    assert_same_pattern(G1, ref.inner.G)
+    assert max_rel(A1.blocks, ref.A1.blocks) <= TOL_FSAI
+    assert max_rel(G1.blocks, ref.inner.G.blocks) <= 1e3 * TOL_FSAI
+    del torch
+
+
 # --------------------------------------------------------------------------- single steps
 
 def test_single_steps_match_oracle(lib, ctx, static_pair, small_biharmonic):
