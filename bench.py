@@ -57,6 +57,24 @@ def algorithmic_bytes(info, smooth_bytes, g_bytes, vec_bytes, iterate_bytes):
     }
 
 
+def profiled_traffic(profile="profiles/cheb4_gt_sell_biharmonic256.md",
+                     sources=("paper_2509_06744_gb300/csrc/sell.cu", "paper_2509_06744_gb300/csrc/kernels_common.cuh")):
+    """DRAM bytes per launch of the roofline kernel from its committed ncu summary, or None when
+    the kernel sources have changed since that capture (the summary records their hash)."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, profile)).read()
+        h = hashlib.sha256()
+        for s in sources:
+            h.update(open(os.path.join(ROOT, s), "rb").read())
+        if f"kernel_source_sha256: {h.hexdigest()}" not in text:
+            return None
+        return int(re.search(r"traffic_bytes_per_launch: (\d+)", text).group(1))
+    except (OSError, AttributeError):
+        return None
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -332,7 +350,8 @@ def main():
         "setup_s": {"assembly_and_galerkin": t_asm, "fsai_lanczos_fp64": t_fsai},
         "kernels_finest": kernels,
         "roofline": {"kernel": "gt: G^T t + Chebyshev-4 update, finest level, FP32", "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": profiled_traffic(),
                      "peak_source": peak_kind, "algorithmic_bytes_per_launch": ab["gt"], "launches_timed": n_l,
                      "largest_total_class": dom},
         "cpu_baseline": cpu,
