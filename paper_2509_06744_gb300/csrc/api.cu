@@ -147,7 +147,7 @@ void finalize_smoother(pum_ctx* ctx, pum_hier* h) {
     if (vdt == PUM_F32) bsr_convert(L.As, L.A, PUM_F32, s);
     if (vdt == PUM_F32 && h->sell)
       for (Bsr* m : {&L.As, &L.G, &L.GT, &L.F0, &L.F0T, &L.G1, &L.G1T, &L.Ps, &L.PTs})
-        if (!m->empty() && m->n_brows >= kSellMinRows) sell_build(*m, s);
+        if (!m->empty() && m->n_brows >= kSellMinRows) sell_build(*m, s, ctx->sm_count);
     for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e}) *v = dalloc(vs * N);
     if (vdt == PUM_F32 && l > 0 && (l < h->sp.mixed_levels || l == nl - 1)) {
       L.b64 = (double*)dalloc(sizeof(double) * N);

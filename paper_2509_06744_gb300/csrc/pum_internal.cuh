@@ -46,7 +46,7 @@ struct DevStatus {
   int where;  // which kernel family (see kWhere*)
   int pad;
 };
-enum { kWhereFsai = 1, kWhereCoarse = 2, kWhereAdaptive = 3, kWhereLanczos = 4 };
+enum { kWhereFsai = 1, kWhereCoarse = 2, kWhereAdaptive = 3, kWhereLanczos = 4, kWhereSell = 5 };
 
 __device__ inline void set_status(DevStatus* s, int code, int info, int where) {
   if (atomicCAS(&s->code, 0, code) == 0) {
@@ -90,11 +90,11 @@ struct Bsr {
 
 void bsr_free(Bsr& m);
 // Sliced layout (sell.cu): build for a FP32/BF16 matrix; product through it (false: not applicable).
-void sell_build(Bsr& m, cudaStream_t s);
+void sell_build(Bsr& m, cudaStream_t s, int sm_count);
 void sell_free(Sell& s);
 bool sell_mv(pum_ctx* ctx, const Bsr& M, int vdt, const void* x, int epi, const struct EpiArgs& e);
-constexpr int kSellMinRows = 32768;  // levels with at least this many block rows use it (one thread
-                                      // per output then fills the GPU)
+constexpr int kSellMinRows = 4096;  // levels with at least this many block rows use it (groups of
+                                     // 8..32 rows then still give about four CTAs per SM)
 // Allocate a device BSR with the given host pattern (values uninitialised).
 void bsr_alloc(Bsr& m, int n_brows, int n_bcols, int d, int dt, const std::vector<int>& rp,
                const std::vector<int>& ci);

@@ -1,106 +1,194 @@
-// Sliced block layout for the smoother's products on large levels.
+// Sliced block layout for the smoother's products on large levels, streamed through shared
+// memory by bulk asynchronous copies.
 //
-// Block rows are grouped by R; group g stores S_g slots, S_g = its longest block row, and
-// slot s of row j holds that row's s-th block (padding: column -1, never read).  The
-// values of (group, slot, block column index c) are stored contiguously over the group's
-// R*d output unknowns, so the R*d threads of a CTA (thread = output unknown) read each
-// (slot, c) as one coalesced run: a warp's load is one 128-byte segment (FP32), with no
-// reliance on L1 to merge the strided row slices of the block-row-major layout.  Padding
-// slots cost memory but no bandwidth.  The fused epilogues are those of the BSR kernel.
+// Layout: block rows are grouped by R; group g stores S_g slots (S_g = its longest block row),
+// and slot s of row j holds that row's s-th block (padding: column -1, zero values).  The values
+// of one (group, slot) form a contiguous chunk of d x (R d) values ordered (block column c,
+// output unknown j d + r), so one cp.async.bulk moves a chunk into shared memory, where the
+// thread of output unknown t reads element c (R d) + t: conflict-free.
+//
+// Kernel: warp 0 is the producer.  Its lane 0 streams the group's chunks into a ring of NS
+// shared-memory stages; stage k is guarded by full[k] (completes when the chunk's bytes have
+// landed) and empty[k] (one arrival per consumer warp once the chunk has been read).  The other
+// warps are consumers: the thread of output unknown j d + r accumulates
+// sum_c A_j[r][c] x[col d + c] over the slots, loading the next slot's x segment while the
+// current chunk lands.  The bytes in flight per SM are then set by shared memory, not by
+// registers.  Every wait is bounded: on expiry the kernel records PUM_ERR_TIMEOUT in the
+// context's status word, drains its own copies (bounded) and returns.  Padding slots read
+// column 0 against zero values, which keeps the loop branch-free.  The fused epilogues are those
+// of the block-row kernel.
 #include <algorithm>
 
 #include "kernels_common.cuh"
 
 namespace pum {
 
-template <int D> constexpr int sell_rows() { return D <= 3 ? 64 : D <= 10 ? 32 : 16; }
+namespace {
 
-int sell_rows_for(int d) {
-  switch (d) {
-    case 3: return sell_rows<3>();
-    case 6: return sell_rows<6>();
-    case 10: return sell_rows<10>();
-    case 15: return sell_rows<15>();
-    case 21: return sell_rows<21>();
-    default: return 0;
-  }
+constexpr int kWaitLimit = 1 << 22;  // polls of an mbarrier before a wait gives up
+constexpr int kHeader = 128;         // bytes for up to 8 full/empty barrier pairs
+constexpr int kMaxStages = 4;
+constexpr int kSellMaxThreads = 32 + 352;  // producer warp + the largest consumer group (d = 21, R = 16)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-// L lanes per output unknown split a group's slots (lane k takes slots s0 + k, s0 + k + L, ...);
-// the partial sums meet in shared memory.  L = 2 lets a level with fewer rows fill the GPU.
-// The group's column indices are staged in shared memory first, so the loads of a slot do
-// not wait on its index, and two slots' loads are issued before their FMAs.  Padding slots
-// (column -1) read column 0 against zero values, which keeps the loop branch-free.
-template <int D, int R, int L, typename MT, typename XT, typename YT, typename X2T, int EPI>
-__global__ void __launch_bounds__(R * D * L) k_sell_mv(int n_brows, const int* __restrict__ goff,
-                                                       const int* __restrict__ cols, const MT* __restrict__ vals,
-                                                       const XT* __restrict__ x, EpiArgs e) {
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of the given parity to complete; false if it did not within the limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (int i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to this
+// CTA's shared memory, completing on `bar` as transaction bytes.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+}  // namespace
+
+// Largest group size R for block size d (bounded by the CTA size and the chunk's shared memory).
+int sell_rows_max(int d) { return d <= 3 ? 64 : d <= 10 ? 32 : 16; }
+
+template <int D, typename MT, typename XT, typename YT, typename X2T, int EPI>
+__global__ void __launch_bounds__(kSellMaxThreads) k_sell_mv(int n_brows, int R, int NS, const int* __restrict__ goff,
+                                                             const int* __restrict__ cols, const MT* __restrict__ vals,
+                                                             const XT* __restrict__ x, EpiArgs e, DevStatus* st) {
   using AT = typename AccOf<MT>::type;
-  constexpr int RD = R * D;
-  extern __shared__ int scol[];  // (s1 - s0) * R column indices of this group
-  __shared__ AT red[L > 1 ? (L - 1) * RD : 1];
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int RD = R * D;
+  const int chunk_elems = D * RD;
+  const uint32_t chunk = (uint32_t)(chunk_elems * (int)sizeof(MT));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* empty = full + kMaxStages;
+  MT* stage = reinterpret_cast<MT*>(smem + kHeader);
+  int* scol = reinterpret_cast<int*>(smem + kHeader + (size_t)NS * chunk);
   const int g = blockIdx.x;
-  const int lane = threadIdx.x / RD;
-  const int t = threadIdx.x - lane * RD;  // j * D + r
-  const int j = t / D;
-  const int row = g * R + j;
-  const bool active = row < n_brows;
-  const int s0 = goff[g], s1 = goff[g + 1];
-  for (int i = threadIdx.x; i < (s1 - s0) * R; i += blockDim.x) scol[i] = max(__ldg(cols + (int64_t)s0 * R + i), 0);
+  const int s0 = goff[g], ns = goff[g + 1] - s0;
+  const int n_consumer_warps = (int)(blockDim.x >> 5) - 1;
+  const MT* src = vals + (int64_t)s0 * chunk_elems;
+
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(full + k, 1);
+      mbar_init(empty + k, (uint32_t)n_consumer_warps);
+    }
+    mbar_fence_init();
+    for (int s = 0; s < min(NS, ns); ++s) {
+      mbar_expect_tx(full + s, chunk);
+      bulk_g2s(stage + (size_t)s * chunk_elems, src + (int64_t)s * chunk_elems, chunk, full + s);
+    }
+  }
+  for (int i = threadIdx.x; i < ns * R; i += blockDim.x) scol[i] = max(__ldg(cols + (int64_t)s0 * R + i), 0);
   __syncthreads();
-  AT acc = 0;
-  if (active) {
-    const MT* v = vals + (int64_t)s0 * D * RD + t;
-    int s = lane;
-    const int ns = s1 - s0;
-    for (; s + L < ns; s += 2 * L) {
-      const int c0 = scol[s * R + j], c1 = scol[(s + L) * R + j];
-      AT a0[D], a1[D], x0[D], x1[D];
-#pragma unroll
-      for (int cc = 0; cc < D; ++cc) {
-        a0[cc] = (AT)to_f(__ldg(v + ((int64_t)s * D + cc) * RD));
-        a1[cc] = (AT)to_f(__ldg(v + ((int64_t)(s + L) * D + cc) * RD));
+
+  if (threadIdx.x < 32) {  // producer warp
+    if (threadIdx.x != 0) return;
+    bool ok = true;
+    int issued = min(NS, ns);
+    for (int s = NS; s < ns; ++s) {
+      const int k = s % NS;
+      if (!mbar_wait(empty + k, (uint32_t)((s / NS) - 1) & 1u)) {
+        ok = false;
+        break;
       }
-      load_row<D>(x + (int64_t)c0 * D, x0);
-      load_row<D>(x + (int64_t)c1 * D, x1);
-#pragma unroll
-      for (int cc = 0; cc < D; ++cc) acc = fma(a0[cc], x0[cc], acc);
-#pragma unroll
-      for (int cc = 0; cc < D; ++cc) acc = fma(a1[cc], x1[cc], acc);
+      mbar_expect_tx(full + k, chunk);
+      bulk_g2s(stage + (size_t)k * chunk_elems, src + (int64_t)s * chunk_elems, chunk, full + k);
+      issued = s + 1;
     }
-    if (s < ns) {
-      const int c0 = scol[s * R + j];
-      AT xv[D];
-      load_row<D>(x + (int64_t)c0 * D, xv);
+    for (int s = max(issued - NS, 0); s < issued; ++s)  // own copies still in flight
+      if (!mbar_wait(full + s % NS, (uint32_t)(s / NS) & 1u)) ok = false;
+    if (!ok) set_status(st, PUM_ERR_TIMEOUT, g, kWhereSell);
+    return;
+  }
+
+  const int t = (int)threadIdx.x - 32;
+  const bool computes = t < RD;
+  const int j = computes ? t / D : 0;
+  const int r = t - j * D;
+  AT acc = 0;
+  AT xn[D];
+  if (computes && ns > 0) load_row<D>(x + (int64_t)scol[j] * D, xn);
+  for (int s = 0; s < ns; ++s) {
+    const int k = s % NS;
+    AT xv[D];
 #pragma unroll
-      for (int cc = 0; cc < D; ++cc) acc = fma((AT)to_f(__ldg(v + ((int64_t)s * D + cc) * RD)), xv[cc], acc);
+    for (int cc = 0; cc < D; ++cc) xv[cc] = xn[cc];
+    if (computes && s + 1 < ns) load_row<D>(x + (int64_t)scol[(s + 1) * R + j] * D, xn);
+    if (!__all_sync(0xffffffffu, mbar_wait(full + k, (uint32_t)(s / NS) & 1u))) {
+      if ((threadIdx.x & 31) == 0) set_status(st, PUM_ERR_TIMEOUT, g, kWhereSell);
+      return;
     }
-  }
-  if constexpr (L > 1) {
-    if (lane > 0) red[(lane - 1) * RD + t] = acc;
-    __syncthreads();
-    if (lane > 0) return;
+    if (computes) {
+      const MT* a = stage + (size_t)k * chunk_elems + t;
 #pragma unroll
-    for (int k = 1; k < L; ++k) acc += red[(k - 1) * RD + t];
+      for (int cc = 0; cc < D; ++cc) acc = fma((AT)to_f(a[cc * RD]), xv[cc], acc);
+    }
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(empty + k);
   }
-  if (!active) return;
-  epilogue<EPI, AT, XT, YT, X2T>(e, (int64_t)row * D + (t - j * D), acc);
+  const int row = g * R + j;
+  if (computes && row < n_brows) epilogue<EPI, AT, XT, YT, X2T>(e, (int64_t)row * D + r, acc);
 }
 
-template <int D, int L, typename MT, typename XT, typename YT, typename X2T>
-static void sell_launch_l(pum_ctx* ctx, const Bsr& M, const void* x, int epi, const EpiArgs& e) {
-  constexpr int R = sell_rows<D>();
-  const dim3 grid(M.sell.n_groups), block(R * D * L);
-  const size_t smem = sizeof(int) * (size_t)M.sell.max_slots * R;
-  const MT* v = (const MT*)M.sell.vals;
+// Ring depth: as many stages as fit in about 40 KB, between 2 and 4.
+static int sell_stages(size_t chunk) { return (int)std::max<size_t>(2, std::min<size_t>(kMaxStages, 40960 / chunk)); }
+
+static size_t sell_smem(const Sell& S, int d, size_t vsize) {
+  const size_t chunk = vsize * (size_t)d * S.R * d;
+  return kHeader + (size_t)sell_stages(chunk) * chunk + sizeof(int) * (size_t)S.max_slots * S.R;
+}
+
+template <int D, typename MT, typename XT, typename YT, typename X2T>
+static void sell_launch(pum_ctx* ctx, const Bsr& M, const void* x, int epi, const EpiArgs& e) {
+  const Sell& S = M.sell;
+  if (S.n_groups == 0) return;
+  const int RD = S.R * D;
+  const unsigned threads = 32u + (unsigned)((RD + 31) / 32) * 32u;
+  const size_t chunk = sizeof(MT) * (size_t)D * RD;
+  const int NS = sell_stages(chunk);
+  const size_t smem = sell_smem(S, D, sizeof(MT));
+  const MT* v = (const MT*)S.vals;
   const XT* xv = (const XT*)x;
   cudaStream_t s = ctx->stream;
   switch (epi) {
-#define PUM_SELL_CASE(E)                                                                                 \
-  case E:                                                                                                \
-    k_sell_mv<D, R, L, MT, XT, YT, X2T, E><<<grid, block, smem, s>>>(M.n_brows, M.sell.goff, M.sell.cols, v, \
-                                                                 xv, e);                                 \
-    break;
+#define PUM_SELL_CASE(E)                                                                                    \
+  case E: {                                                                                                 \
+    auto kern = k_sell_mv<D, MT, XT, YT, X2T, E>;                                                           \
+    if (smem > 48 * 1024)                                                                                   \
+      PUM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));        \
+    kern<<<S.n_groups, threads, smem, s>>>(M.n_brows, S.R, NS, S.goff, S.cols, v, xv, e, ctx->status);       \
+    break;                                                                                                  \
+  }
     PUM_SELL_CASE(EPI_SET)
     PUM_SELL_CASE(EPI_RESID)
     PUM_SELL_CASE(EPI_ADD)
@@ -113,15 +201,6 @@ static void sell_launch_l(pum_ctx* ctx, const Bsr& M, const void* x, int epi, co
   }
   count_launch(ctx);
   PUM_CUDA(cudaGetLastError());
-}
-
-template <int D, typename MT, typename XT, typename YT, typename X2T>
-static void sell_launch(pum_ctx* ctx, const Bsr& M, const void* x, int epi, const EpiArgs& e) {
-  // two lanes per output when one would leave the GPU under-filled (about sm_count x 2048 threads)
-  if ((int64_t)M.n_brows * D < (int64_t)ctx->sm_count * 1536)
-    sell_launch_l<D, 2, MT, XT, YT, X2T>(ctx, M, x, epi, e);
-  else
-    sell_launch_l<D, 1, MT, XT, YT, X2T>(ctx, M, x, epi, e);
 }
 
 template <int D>
@@ -181,11 +260,15 @@ void sell_free(Sell& s) {
   s = Sell();
 }
 
-void sell_build(Bsr& M, cudaStream_t st) {
+// R: the largest power of two <= sell_rows_max(d), and >= 8, that still gives about four groups
+// per SM (one CTA per group).  R d^2 values per slot then make every chunk a multiple of 16 bytes.
+void sell_build(Bsr& M, cudaStream_t st, int sm_count) {
   sell_free(M.sell);
-  const int R = sell_rows_for(M.d);
-  if (!R || M.dt == PUM_F64) return;
-  const int n = M.n_brows, d = M.d;
+  const int d = M.d;
+  if (M.dt == PUM_F64 || !(d == 3 || d == 6 || d == 10 || d == 15 || d == 21)) return;
+  const int n = M.n_brows;
+  int R = sell_rows_max(d);
+  while (R > 8 && (int64_t)((n + R - 1) / R) < 4LL * sm_count) R /= 2;
   const int ng = (n + R - 1) / R;
   std::vector<int> goff(ng + 1, 0);
   for (int g = 0; g < ng; ++g) {
@@ -205,7 +288,16 @@ void sell_build(Bsr& M, cudaStream_t st) {
       }
     }
   Sell& S = M.sell;
-  const size_t vbytes = dt_size(M.dt) * (size_t)std::max<int64_t>(slots, 1) * R * d * d;
+  S.R = R;
+  S.n_groups = ng;
+  S.slots = slots;
+  S.max_slots = 0;
+  for (int g = 0; g < ng; ++g) S.max_slots = std::max(S.max_slots, goff[g + 1] - goff[g]);
+  const size_t vsize = dt_size(M.dt);
+  PUM_CHECK((vsize * (size_t)d * R * d) % 16 == 0, PUM_ERR_UNSUPPORTED, "sliced layout: chunk not 16-byte sized");
+  PUM_CHECK(sell_smem(S, d, vsize) <= 200 * 1024, PUM_ERR_UNSUPPORTED, "sliced layout: row too long");
+  S.R = 0;  // set again once the device arrays exist
+  const size_t vbytes = vsize * (size_t)std::max<int64_t>(slots, 1) * R * d * d;
   if (cudaMalloc(&S.goff, sizeof(int) * goff.size()) != cudaSuccess ||
       cudaMalloc(&S.cols, sizeof(int) * std::max<size_t>(cols.size(), 1)) != cudaSuccess ||
       cudaMalloc(&S.vals, vbytes) != cudaSuccess) {
@@ -234,11 +326,6 @@ void sell_build(Bsr& M, cudaStream_t st) {
   PUM_CUDA(cudaStreamSynchronize(st));
   cudaFree(dsrc);
   S.R = R;
-  S.n_groups = ng;
-  S.slots = slots;
-  S.max_slots = 0;
-  for (int g = 0; g < ng; ++g) S.max_slots = std::max(S.max_slots, goff[g + 1] - goff[g]);
-  PUM_CHECK((size_t)S.max_slots * R * sizeof(int) <= 32768, PUM_ERR_UNSUPPORTED, "sliced layout: row too long");
 }
 
 }  // namespace pum

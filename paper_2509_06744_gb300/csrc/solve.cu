@@ -367,6 +367,18 @@ void vcycle_apply_impl(pum_ctx* ctx, pum_hier* h, const double* r, double* z) {
   if (ctx->timing) graph_harvest(ctx, h);  // timing mode: collect before returning
 }
 
+// Device status word after the stream has drained: a kernel that recorded an error (a bounded
+// wait that expired) turns into that status.
+static void check_device_status(pum_ctx* ctx) {
+  DevStatus st{};
+  PUM_CUDA(cudaMemcpyAsync(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
+  PUM_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (!st.code) return;
+  PUM_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), ctx->stream));
+  throw Error{(pum_status)st.code, "device status " + std::to_string(st.code) + " in kernel family " +
+                                       std::to_string(st.where) + " at " + std::to_string(st.info)};
+}
+
 pum_status pcg_impl(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_report* rep) {
   Level& L0 = h->lv[0];
   const int64_t N = (int64_t)L0.n * L0.d;
@@ -407,6 +419,7 @@ pum_status pcg_impl(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_r
     const double pq = ctx->h_scal[S_PQ], rr = ctx->h_scal[S_RR], rz = ctx->h_scal[S_RZ];
     if (!(pq > 0.0) || !std::isfinite(rr) || !std::isfinite(rz)) {
       rep->iters = it;
+      check_device_status(ctx);
       throw Error{PUM_ERR_BREAKDOWN, "PCG breakdown: p^T A p = " + std::to_string(pq) + ", r^T z = " +
                                          std::to_string(rz)};
     }
@@ -417,6 +430,7 @@ pum_status pcg_impl(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_r
     if (rel <= rep->rtol) {
       rep->converged = 1;
       graph_harvest(ctx, h);
+      check_device_status(ctx);
       return PUM_OK;
     }
     if (rep->flexible) PUM_CUDA(cudaMemcpyAsync(zo, z, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
@@ -429,6 +443,7 @@ pum_status pcg_impl(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_r
     PUM_CUDA(cudaGetLastError());
   }
   graph_harvest(ctx, h);
+  check_device_status(ctx);
   return PUM_ERR_NOCONV;
 }
 

@@ -340,13 +340,13 @@ def test_block_sizes_residual_and_static_fsai(lib, ctx, d):
     assert max_rel(G.blocks, ref.G.blocks) <= TOL_FSAI
 
 
-@pytest.mark.parametrize("d", [6, 10, 21])
-def test_sliced_layout_products_on_large_levels(lib, d):
-    """Levels with >= 32768 block rows smooth through the sliced block layout: same results as
-    the block-row kernel (FP32 rounding) and as the FP64 Algorithm 3 of the oracle."""
+@pytest.mark.parametrize("d,side", [(6, 182), (10, 182), (21, 182), (10, 90), (21, 70)])
+def test_sliced_layout_products_on_large_levels(lib, d, side):
+    """Levels with >= 4096 block rows smooth through the sliced block layout (groups of 32, 16 or
+    8 rows, each with a ragged last group here): same results as the block-row kernel (FP32
+    rounding) and as the FP64 Algorithm 3 of the oracle."""
     import os
     import torch
-    side = 182  # 33,124 block rows
     A = _random_block_spd(side, d, seed=3 + d)
     P = bk.from_blocks(A.n_rows, 1, d, {(i, 0): np.eye(d) for i in range(A.n_rows)})
     N = A.n_rows * d
