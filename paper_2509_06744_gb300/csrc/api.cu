@@ -59,16 +59,18 @@ void free_level(Level& L) {
   for (Bsr* m : {&L.A, &L.As, &L.P, &L.PT, &L.Ps, &L.PTs, &L.G, &L.GT, &L.G64, &L.F0, &L.F0T, &L.F064, &L.G164,
                  &L.A1, &L.G1, &L.G1T})
     bsr_free(*m);
-  for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e, (void**)&L.b64, (void**)&L.z64})
+  for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e, (void**)&L.b64, (void**)&L.z64, &L.zs})
     if (*v) { cudaFree(*v); *v = nullptr; }
+  sell_free(L.Adf);
 }
 
 void free_smoother(pum_hier* h) {
   graph_destroy(h->vgraph);
   for (auto& L : h->lv) {
     for (Bsr* m : {&L.As, &L.PT, &L.Ps, &L.PTs, &L.G, &L.GT, &L.F0, &L.F0T, &L.G1, &L.G1T}) bsr_free(*m);
-    for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e, (void**)&L.b64, (void**)&L.z64})
+    for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e, (void**)&L.b64, (void**)&L.z64, &L.zs})
       if (*v) { cudaFree(*v); *v = nullptr; }
+    sell_free(L.Adf);
   }
   for (auto& w : h->w64)
     if (w) { cudaFree(w); w = nullptr; }
@@ -152,6 +154,10 @@ void finalize_smoother(pum_ctx* ctx, pum_hier* h) {
     if (vdt == PUM_F32 && l > 0 && (l < h->sp.mixed_levels || l == nl - 1)) {
       L.b64 = (double*)dalloc(sizeof(double) * N);
       L.z64 = (double*)dalloc(sizeof(double) * N);
+    }
+    if (vdt == PUM_F32 && h->sell && l < h->sp.mixed_levels && l + 1 < nl && L.n >= kSellMinRows) {
+      sell_build_df(L.Adf, L.A, s, ctx->sm_count);  // accurate residuals in double-float arithmetic
+      L.zs = dalloc(sizeof(float) * 2 * N);
     }
     PUM_CUDA(cudaMemsetAsync(L.x, 0, vs * N, s));
   }

@@ -8,6 +8,7 @@ namespace pum {
 
 template <typename T> struct AccOf { using type = float; };
 template <> struct AccOf<double> { using type = double; };
+template <> struct AccOf<float2> { using type = double; };  // double-float (hi, lo) matrix values
 
 __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ float to_f(float v) { return v; }
@@ -39,6 +40,13 @@ __device__ __forceinline__ void load_row(const T* __restrict__ p, AT (&out)[D]) 
   }
 }
 
+// (hi, lo) FP32 pair with hi + lo = v to 2^-48 relative: the split shadow the double-float
+// products read instead of an FP64 vector.
+__device__ __forceinline__ float2 split_df(double v) {
+  const float hi = __double2float_rn(v);
+  return make_float2(hi, __double2float_rn(v - (double)hi));
+}
+
 // Epilogue of the product acc = (M x)_tid for output unknown tid.
 template <int EPI, typename AT, typename XT, typename YT, typename X2T>
 __device__ __forceinline__ void epilogue(const EpiArgs& e, int64_t tid, AT acc) {
@@ -50,23 +58,38 @@ __device__ __forceinline__ void epilogue(const EpiArgs& e, int64_t tid, AT acc) 
     // b - A x, formed in the accumulation precision (FP64 for an FP64 operator)
     y[tid] = (YT)((AT)((const XT*)e.b)[tid] - acc);
   } else if constexpr (EPI == EPI_ADD) {
-    y[tid] = (YT)((AT)y[tid] + acc);
+    const YT v = (YT)((AT)y[tid] + acc);
+    y[tid] = v;
+    if constexpr (sizeof(YT) == 8)
+      if (e.ys) ((float2*)e.ys)[tid] = split_df((double)v);
   } else if constexpr (EPI == EPI_CHEB_FIRST0) {
     YT* xo = (YT*)e.xo;
     y[tid] = (YT)acc;
     xo[tid] = (YT)((AT)e.dmu * acc);
-    if (x2) x2[tid] = e.x2_set ? (X2T)(e.dmu * (double)acc) : (X2T)((double)x2[tid] + e.dmu * (double)acc);
+    if (x2) {
+      const X2T v = e.x2_set ? (X2T)(e.dmu * (double)acc) : (X2T)((double)x2[tid] + e.dmu * (double)acc);
+      x2[tid] = v;
+      if (e.x2s) ((float2*)e.x2s)[tid] = split_df((double)v);
+    }
   } else if constexpr (EPI == EPI_CHEB_FIRST) {
     YT* xo = (YT*)e.xo;
     y[tid] = (YT)acc;
     xo[tid] = (YT)((AT)xo[tid] + (AT)e.dmu * acc);
-    if (x2) x2[tid] = (X2T)((double)x2[tid] + e.dmu * (double)acc);
+    if (x2) {
+      const X2T v = (X2T)((double)x2[tid] + e.dmu * (double)acc);
+      x2[tid] = v;
+      if (e.x2s) ((float2*)e.x2s)[tid] = split_df((double)v);
+    }
   } else if constexpr (EPI == EPI_CHEB) {
     YT* xo = (YT*)e.xo;
     const AT pn = (AT)e.mu2 * (AT)y[tid] + acc;
     y[tid] = (YT)pn;
     xo[tid] = (YT)((AT)xo[tid] + (AT)e.dmu * pn);
-    if (x2) x2[tid] = (X2T)((double)x2[tid] + e.dmu * (double)pn);
+    if (x2) {
+      const X2T v = (X2T)((double)x2[tid] + e.dmu * (double)pn);
+      x2[tid] = v;
+      if (e.x2s) ((float2*)e.x2s)[tid] = split_df((double)v);
+    }
   }
 }
 

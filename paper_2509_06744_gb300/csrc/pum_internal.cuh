@@ -93,6 +93,12 @@ void bsr_free(Bsr& m);
 void sell_build(Bsr& m, cudaStream_t s, int sm_count);
 void sell_free(Sell& s);
 bool sell_mv(pum_ctx* ctx, const Bsr& M, int vdt, const void* x, int epi, const struct EpiArgs& e);
+// Sliced layout of an FP64 matrix as FP32 pairs (hi = fl32(a), lo = fl32(a - hi)), and its
+// product with a split vector (float2 hi, lo per unknown) in double-float arithmetic: RESID
+// into an FP32 y with an FP64 b, or ADD into an FP64 y.
+void sell_build_df(Sell& S, const Bsr& M64, cudaStream_t s, int sm_count);
+void sell_df_mv(pum_ctx* ctx, const Sell& S, int d, int n_brows, const void* xs, int epi, const struct EpiArgs& e,
+                int tk = -1);
 constexpr int kSellMinRows = 4096;  // levels with at least this many block rows use it (groups of
                                      // 8..32 rows then still give about four CTAs per SM)
 // Allocate a device BSR with the given host pattern (values uninitialised).
@@ -135,6 +141,10 @@ struct Level {
   void *x = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *t = nullptr, *u = nullptr;
   void *c = nullptr, *e = nullptr;  // correction-form post-smoothing: rhs c = b - A x, iterate e
   double *b64 = nullptr, *z64 = nullptr;  // FP64 right-hand side and iterate of a mixed level
+  // Mixed level on the sliced layout: A as FP32 pairs (hi + lo) for the accurate residuals, and
+  // the split (hi, lo) shadow of the level's FP64 iterate that those products read.
+  Sell Adf;
+  void* zs = nullptr;
 };
 
 struct Coarse {
@@ -220,6 +230,8 @@ struct EpiArgs {
   bool x2_set = false;       // CHEB_FIRST0: x2 <- dmu p instead of x2 += dmu p
   double* partials = nullptr;  // DOT: per-CTA partial sums of acc * x
   int xdt = -1, ydt = -1, x2dt = -1;  // vector dtypes when they differ from the call's vdt
+  void* x2s = nullptr;  // CHEB*: float2 (hi, lo) split shadow of the FP64 second iterate, written with it
+  void* ys = nullptr;   // ADD into an FP64 y: float2 split shadow of y, written with it
 };
 
 // y (by epilogue) = M x for a BSR matrix; vector dtype vdt (F64 or F32).
@@ -244,7 +256,7 @@ void coarse_factor(pum_ctx* ctx, pum_hier* h);
 // Smoother / cycle (solve.cu)
 void apply_M(pum_ctx* ctx, pum_hier* h, int l, const void* r, void* z, int tk_first);
 void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_zero, void* x_acc, int acc_dt,
-           bool acc_set);
+           bool acc_set, void* x_acc_split = nullptr);
 void vcycle_level(pum_ctx* ctx, pum_hier* h, int l);
 void coarse_solve(pum_ctx* ctx, pum_hier* h, const void* b, void* x, int vdt);
 

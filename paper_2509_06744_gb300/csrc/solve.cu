@@ -75,7 +75,7 @@ void apply_M(pum_ctx* ctx, pum_hier* h, int l, const void* r, void* z, int) {
 // Algorithm 3 on level l for A x = rhs with iterate x (in place); x_zero: x0 = 0.  When
 // x_acc is given, every update of x is also added to x_acc (the correction form below).
 void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_zero, void* x_acc, int acc_dt,
-           bool acc_set) {
+           bool acc_set, void* x_acc_split) {
   Level& L = h->lv[l];
   const int vdt = h->smooth_dt;
   const int k = h->sp.degree_k;
@@ -94,6 +94,7 @@ void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_ze
     e.y = L.p;
     e.xo = x;
     e.xo2 = x_acc;
+    e.x2s = x_acc_split;
     e.x2dt = acc_dt;
     e.x2_set = acc_set && x_zero && i == 1;
     e.dmu = dd * h->mu[i - 1];
@@ -266,6 +267,17 @@ static bool is_mixed(const pum_hier* h, int l) {
   return h->smooth_dt == PUM_F32 && l < h->sp.mixed_levels;
 }
 
+// y = b - A z with FP64 b and z, FP32 y, to FP64 accuracy: on the sliced layout in double-float
+// arithmetic (A as FP32 pairs, z read through its split shadow, which every writer of z on this
+// level keeps current), else with the FP64 operator.
+static void accurate_residual(pum_ctx* ctx, Level& L, const double* z, const EpiArgs& e, int tk) {
+  if (L.Adf.R) {
+    sell_df_mv(ctx, L.Adf, L.d, L.n, L.zs, EPI_RESID, e, tk);
+    return;
+  }
+  bsr_mv(ctx, L.A, PUM_F32, z, EPI_RESID, e, tk);
+}
+
 static void vcycle_mixed(pum_ctx* ctx, pum_hier* h, int l, const double* r, double* z) {
   Level& L = h->lv[l];
   const int64_t N = (int64_t)L.n * L.d;
@@ -275,14 +287,14 @@ static void vcycle_mixed(pum_ctx* ctx, pum_hier* h, int l, const double* r, doub
   }
   Level& C = h->lv[l + 1];
   const int tk = l == 0 ? PUM_TK_RESID64 : -1;
-  convert_vec(ctx, L.b, PUM_F32, r, PUM_F64, N);       // FP32 right-hand side of the smoother
-  cheb4(ctx, h, l, L.b, L.e, true, z, PUM_F64, true);  // pre-smoothing: z = e in FP64
+  convert_vec(ctx, L.b, PUM_F32, r, PUM_F64, N);             // FP32 right-hand side of the smoother
+  cheb4(ctx, h, l, L.b, L.e, true, z, PUM_F64, true, L.zs);  // pre-smoothing: z = e in FP64
   EpiArgs er{};
   er.y = L.r;
   er.b = r;
   er.xdt = PUM_F64;
   er.ydt = PUM_F32;
-  bsr_mv(ctx, L.A, PUM_F32, z, EPI_RESID, er, tk);  // r_f = r - A z
+  accurate_residual(ctx, L, z, er, tk);  // r_f = r - A z
   EpiArgs rs{};
   rs.y = C.b;
   bsr_mv(ctx, L.PTs, PUM_F32, L.r, EPI_SET, rs);  // b_c = P^T r_f
@@ -292,10 +304,12 @@ static void vcycle_mixed(pum_ctx* ctx, pum_hier* h, int l, const double* r, doub
     convert_vec(ctx, C.b64, PUM_F64, C.b, PUM_F32, Nc);
     vcycle_mixed(ctx, h, l + 1, C.b64, C.z64);
     pa.y = z;
+    pa.ys = L.zs;
     bsr_mv(ctx, L.P, PUM_F64, C.z64, EPI_ADD, pa);  // z += P z_c (FP64)
   } else {
     vcycle_level(ctx, h, l + 1);
     pa.y = z;
+    pa.ys = L.zs;
     pa.ydt = PUM_F64;
     bsr_mv(ctx, L.Ps, PUM_F32, C.x, EPI_ADD, pa);  // z += P x_c
   }
@@ -304,7 +318,7 @@ static void vcycle_mixed(pum_ctx* ctx, pum_hier* h, int l, const double* r, doub
   cr.b = r;
   cr.xdt = PUM_F64;
   cr.ydt = PUM_F32;
-  bsr_mv(ctx, L.A, PUM_F32, z, EPI_RESID, cr, tk);     // c = r - A z
+  accurate_residual(ctx, L, z, cr, tk);                 // c = r - A z
   cheb4(ctx, h, l, L.c, L.e, true, z, PUM_F64, false);  // A e = c from 0; z += updates
 }
 

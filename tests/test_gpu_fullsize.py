@@ -142,3 +142,75 @@ def test_vcycle_symmetric_and_pcg_forms_agree(gpu):
     r = torch.zeros_like(b)
     H.residual(0, b, x32, r)
     assert float(torch.linalg.norm(r) / torch.linalg.norm(b)) <= 1e-5  # FP64 rounding floor of A x here
+
+
+# ---------------------------------------------------------------------------- triharmonic, p = 5
+
+TRI = pin.TRIHARMONIC_256
+TRI_SAMPLE = [0, 255, 65535, 128 * 256 + 128, 40000]
+
+
+@pytest.fixture(scope="module")
+def tri():
+    """256x256-patch triharmonic (d = 21, 1,376,256 unknowns) with the nested adaptive FSAI."""
+    import torch
+    import paper_2509_06744_gb300 as L
+    ctx = L.Context(0)
+    b = torch.zeros(TRI.n_dofs, dtype=torch.float64, device="cuda")
+    H = L.Hierarchy.assemble(ctx, TRI.equation, TRI.p, TRI.finest_m, TRI.n_levels,
+                             f_coef=pin.fourier_coefficients(TRI.rhs_seed), f_decay=TRI.rhs_decay,
+                             nitsche=TRI.nitsche, b=b)
+    A0 = from_export(H.export(0, L.PUM_MAT_A))
+    H.setup(p0=TRI.fsai_p0, adaptive=True, t_max=TRI.t_max, tau=TRI.tau, nested=True, k=TRI.cheb_k)
+    yield L, ctx, H, b, A0
+    H.close()
+    ctx.close()
+
+
+def _tri_rows(rows):
+    f = pum.fourier_source(pin.fourier_coefficients(TRI.rhs_seed), TRI.rhs_decay)
+    g = pum.nitsche_gamma(TRI.equation, TRI.p, TRI.finest_m, TRI.nitsche)
+    return pum.assemble(TRI.finest_m, TRI.p, TRI.equation, g, f=f, with_mass=False, rows=rows)
+
+
+def test_triharmonic_assembled_rows_match_oracle(tri):
+    L, ctx, H, b, A = tri
+    asm = _tri_rows(TRI_SAMPLE)
+    bh = host(b)
+    scale = np.max(np.abs(A.blocks))
+    d = TRI.d
+    for k in TRI_SAMPLE:
+        assert list(A.row(k)) == list(asm.A.row(k)), f"pattern of row {k}"
+        for j in A.row(k):
+            assert np.max(np.abs(A.block(k, j) - asm.A.block(k, j))) <= TOL_ASSEMBLY * scale
+        assert np.max(np.abs(bh[k * d:(k + 1) * d] - asm.b[k * d:(k + 1) * d])) <= TOL_ASSEMBLY * np.max(np.abs(bh))
+
+
+def test_triharmonic_nested_outer_factor_rows(tri):
+    """F0 of the nested FSAI (Algorithm 1 from the diagonal, t_max = 6): sampled rows bit-exact
+    in pattern against the oracle run on a window of A around the row."""
+    L, ctx, H, b, _ = tri
+    F0 = from_export(H.export(0, L.PUM_MAT_F0))
+    for k in [128 * 256 + 128, 257, 65535]:
+        A = _tri_rows(_window(k, 8, TRI.finest_m)).A
+        Pk = fsai.adaptive_row(A, k, [k], TRI.t_max, TRI.tau)
+        assert list(F0.row(k)) == Pk, f"adaptive pattern of row {k}"
+        ref, _ = fsai.fsai_row(A, k, Pk)  # F = [-Y^T, I] (unscaled), as the nested chain uses it
+        scale = max(np.max(np.abs(v)) for v in ref.values())
+        for j, v in ref.items():
+            assert np.max(np.abs(F0.block(k, j) - v)) <= TOL_FSAI * scale
+
+
+def test_triharmonic_fp64_pcg_converges(tri):
+    """The FP64 form reaches 1e-8 at full size, and its iterates have converged: a solve to
+    1e-10 moves the solution by less than 1e-6 (relative).  The true residual is no measure
+    here: the FP64 rounding of A x alone is ~5e-2 of |b| (penalties of order h^-5)."""
+    import torch
+    L, ctx, H, b, _ = tri
+    x = torch.zeros_like(b)
+    rep = H.pcg(b, x, rtol=1e-8, maxit=100)
+    assert rep["converged"] and rep["iters"] <= 40
+    x2 = torch.zeros_like(b)
+    rep2 = H.pcg(b, x2, rtol=1e-10, maxit=200)
+    assert rep2["converged"]
+    assert float(torch.linalg.norm(x - x2) / torch.linalg.norm(x2)) <= 1e-6

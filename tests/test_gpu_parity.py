@@ -280,6 +280,42 @@ def test_fp32_smoothing_fp64_outer_reaches_tolerance(lib, ctx, small_biharmonic,
     assert norm_rel(xs, ref.x) <= 1e-5
 
 
+def test_fp32_form_double_float_residuals(lib):
+    """64x64 patches: the finest level (4096 block rows) is on the sliced layout, so the FP32
+    form's two accurate residuals per cycle run in double-float arithmetic there.  The solve
+    must match the plain FP64 form (iterations, history, solution) as closely as the same FP32
+    form with FP64-operator residuals (sliced layout off) does."""
+    import os
+    import torch
+    pr = pin.SMALL_BIHARMONIC
+    m, levels = 64, 7
+    out = {}
+    for form in ("f64", "df", "fp64op"):
+        if form == "fp64op":
+            os.environ["PUM_NO_SELL"] = "1"
+        try:
+            c = lib.Context(0)
+        finally:
+            os.environ.pop("PUM_NO_SELL", None)
+        b = torch.zeros(m * m * pr.d, dtype=torch.float64, device="cuda")
+        H = lib.Hierarchy.assemble(c, pr.equation, pr.p, m, levels, f_coef=pin.fourier_coefficients(5),
+                                   f_decay=pr.rhs_decay, nitsche=pr.nitsche, b=b)
+        if form == "f64":
+            H.setup(p0="lower", k=3)
+        else:
+            H.setup(p0="lower", k=3, smooth="f32", g="f32")
+        x = torch.zeros_like(b)
+        rep = H.pcg(b, x, rtol=1e-8, maxit=100, flexible=form != "f64")
+        out[form] = (rep, host(x))
+        H.close()
+        c.close()
+    for form in ("df", "fp64op"):
+        assert out[form][0]["iters"] == out["f64"][0]["iters"]
+        h, h64 = np.array(out[form][0]["history"]), np.array(out["f64"][0]["history"])
+        assert np.max(np.abs(h - h64) / h64) <= 1e-2  # FP32 smoothing perturbs each cycle slightly
+        assert norm_rel(out[form][1], out["f64"][1]) <= 1e-7
+
+
 def test_save_load_roundtrip_bitwise(lib, ctx, static_pair, tmp_path):
     H, _ = static_pair
     path = str(tmp_path / "hier.bin")
