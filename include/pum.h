@@ -17,8 +17,10 @@
  *    context's CUDA stream; calls return after queuing unless stated otherwise.
  *  - Every call returns a pum_status and never aborts.  On failure a message is
  *    available from pum_last_error().  Device-side conditions (non-positive
- *    Cholesky pivot, breakdown) are recorded in a device status word that the
- *    synchronous calls (bfsai_setup, pcg_solve, pum_sync) check before return.
+ *    Cholesky pivot, breakdown, a bounded wait on a shared-memory copy barrier
+ *    that expired: PUM_ERR_TIMEOUT) are recorded in a device status word that
+ *    the synchronous calls (bfsai_setup, pcg_solve, pum_sync) check before
+ *    return.  No kernel traps or spins without a bound.
  *  - Threading: a context is used by one host thread at a time.
  */
 #ifndef PUM_H
