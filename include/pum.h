@@ -110,6 +110,12 @@ typedef struct {
                             with the FP64 operator, FP64 prolongation between such levels);
                             with mixed_levels > 0 the other levels post-smooth in correction
                             form with FP64-operator residuals; 0: plain FP32 cycle           */
+  int32_t fp32_levels;   /* FP32 form: only the first fp32_levels levels store A, P, G and
+                            vectors in FP32 (G in g_dt); the coarser ones smooth in FP64, for
+                            Galerkin operators beyond FP32 (diagonal blocks with condition
+                            numbers near 1/eps_32).  A level count below n_levels needs
+                            fp32_levels <= mixed_levels (the switch happens under a mixed
+                            level); >= n_levels: every level                                   */
 } smoother_params;
 
 /* Outer preconditioned CG (one V(k,k) cycle as preconditioner). */

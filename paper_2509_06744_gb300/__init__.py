@@ -171,11 +171,11 @@ class Hierarchy:
     def setup(self, p0: str = "lower", adaptive: bool = False, t_max: int = 0, tau: float = 1.0,
               nested: bool = False, tie_rel: float = 1e-9, k: int = 2, lanczos_its: int = 100,
               lanczos_safety: float = 1.01, lanczos_seed: int = 0, smooth: str = "f64", g: str | None = None,
-              mixed_levels: int = 64):
+              mixed_levels: int = 64, fp32_levels: int = 64):
         fp = _lib.FsaiParams(PUM_P0_LOWER if p0 == "lower" else PUM_P0_DIAG, int(adaptive), t_max, tau,
                              int(nested), tie_rel)
         sp = _lib.SmootherParams(k, lanczos_its, lanczos_safety, lanczos_seed, _DT[smooth], _DT[g or smooth],
-                                 int(mixed_levels))
+                                 int(mixed_levels), int(fp32_levels))
         self.ctx.check(self.lib.bfsai_setup(self.ctx.h, self.h, C.byref(fp), C.byref(sp)))
 
     def close(self):

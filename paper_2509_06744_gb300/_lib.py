@@ -42,7 +42,8 @@ class FsaiParams(C.Structure):
 
 class SmootherParams(C.Structure):
     _fields_ = [("degree_k", c_int32), ("lanczos_its", c_int32), ("lanczos_safety", c_double),
-                ("lanczos_seed", C.c_uint64), ("smooth_dt", c_int32), ("g_dt", c_int32), ("mixed_levels", c_int32)]
+                ("lanczos_seed", C.c_uint64), ("smooth_dt", c_int32), ("g_dt", c_int32), ("mixed_levels", c_int32),
+                ("fp32_levels", c_int32)]
 
 
 class PcgReport(C.Structure):

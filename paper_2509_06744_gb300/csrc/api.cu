@@ -16,6 +16,12 @@ pum_status pcg_impl(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_r
 
 using namespace pum;
 
+int pum::level_vdt(const pum_hier* h, int l) {
+  return (h->smooth_dt == PUM_F32 && l < h->sp.fp32_levels) ? PUM_F32 : PUM_F64;
+}
+
+int pum::level_gdt(const pum_hier* h, int l) { return level_vdt(h, l) == PUM_F32 ? h->g_dt : PUM_F64; }
+
 namespace {
 
 template <typename F>
@@ -62,6 +68,7 @@ void free_level(Level& L) {
   for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e, (void**)&L.b64, (void**)&L.z64, &L.zs})
     if (*v) { cudaFree(*v); *v = nullptr; }
   sell_free(L.Adf);
+  sell_free(L.Pdf);
 }
 
 void free_smoother(pum_hier* h) {
@@ -71,6 +78,7 @@ void free_smoother(pum_hier* h) {
     for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e, (void**)&L.b64, (void**)&L.z64, &L.zs})
       if (*v) { cudaFree(*v); *v = nullptr; }
     sell_free(L.Adf);
+    sell_free(L.Pdf);
   }
   for (auto& w : h->w64)
     if (w) { cudaFree(w); w = nullptr; }
@@ -124,11 +132,13 @@ void* dalloc(size_t bytes) {
 // transposes, work vectors, Chebyshev mu sequence.
 void finalize_smoother(pum_ctx* ctx, pum_hier* h) {
   cudaStream_t s = ctx->stream;
-  const int vdt = h->smooth_dt;
-  const size_t vs = dt_size(vdt);
   const int nl = (int)h->lv.size();
   for (int l = 0; l < nl; ++l) {
     Level& L = h->lv[l];
+    L.vdt = level_vdt(h, l);
+    L.gdt = level_gdt(h, l);
+    const int vdt = L.vdt;
+    const size_t vs = dt_size(vdt);
     const size_t N = (size_t)L.n * L.d;
     if (l + 1 < nl) {
       bsr_transpose(L.PT, L.P, s);
@@ -137,12 +147,12 @@ void finalize_smoother(pum_ctx* ctx, pum_hier* h) {
         bsr_convert(L.PTs, L.PT, PUM_F32, s);
       }
       if (h->fp.nested) {
-        bsr_convert(L.F0, L.F064, h->g_dt, s);
-        bsr_convert(L.G1, L.G164, h->g_dt, s);
+        bsr_convert(L.F0, L.F064, L.gdt, s);
+        bsr_convert(L.G1, L.G164, L.gdt, s);
         bsr_transpose(L.F0T, L.F0, s);
         bsr_transpose(L.G1T, L.G1, s);
       } else {
-        bsr_convert(L.G, L.G64, h->g_dt, s);
+        bsr_convert(L.G, L.G64, L.gdt, s);
         bsr_transpose(L.GT, L.G, s);
       }
     }
@@ -151,13 +161,18 @@ void finalize_smoother(pum_ctx* ctx, pum_hier* h) {
       for (Bsr* m : {&L.As, &L.G, &L.GT, &L.F0, &L.F0T, &L.G1, &L.G1T, &L.Ps, &L.PTs})
         if (!m->empty() && m->n_brows >= kSellMinRows) sell_build(*m, s, ctx->sm_count);
     for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e}) *v = dalloc(vs * N);
-    if (vdt == PUM_F32 && l > 0 && (l < h->sp.mixed_levels || l == nl - 1)) {
+    if (h->smooth_dt == PUM_F32 && l > 0 && (l < h->sp.mixed_levels || l == nl - 1)) {
       L.b64 = (double*)dalloc(sizeof(double) * N);
       L.z64 = (double*)dalloc(sizeof(double) * N);
     }
-    if (vdt == PUM_F32 && h->sell && l < h->sp.mixed_levels && l + 1 < nl && L.n >= kSellMinRows) {
+    auto df_level = [&](int m) {  // mixed level on the sliced layout: double-float residuals
+      return level_vdt(h, m) == PUM_F32 && h->sell && m < h->sp.mixed_levels && m + 1 < nl &&
+             h->lv[m].n >= kSellMinRows;
+    };
+    if (df_level(l)) {
       sell_build_df(L.Adf, L.A, s, ctx->sm_count);  // accurate residuals in double-float arithmetic
       L.zs = dalloc(sizeof(float) * 2 * N);
+      if (df_level(l + 1)) sell_build_df(L.Pdf, L.P, s, ctx->sm_count);  // z += P z_c from the split z_c
     }
     PUM_CUDA(cudaMemsetAsync(L.x, 0, vs * N, s));
   }
@@ -181,6 +196,7 @@ void check_params(const bfsai_params* fp, const smoother_params* sp) {
   PUM_CHECK(fp->tie_rel >= 0.0, PUM_ERR_INVALID_ARG, "tie_rel must be >= 0");
   PUM_CHECK(sp->degree_k >= 1 && sp->degree_k <= 64, PUM_ERR_INVALID_ARG, "degree_k must be in 1..64");
   PUM_CHECK(sp->lanczos_its >= 1 && sp->lanczos_safety >= 1.0, PUM_ERR_INVALID_ARG, "Lanczos parameters");
+  PUM_CHECK(sp->fp32_levels >= 0, PUM_ERR_INVALID_ARG, "fp32_levels must be >= 0");
   PUM_CHECK(sp->mixed_levels >= 0, PUM_ERR_INVALID_ARG, "mixed_levels must be >= 0");
   PUM_CHECK(sp->smooth_dt == PUM_F64 || sp->smooth_dt == PUM_F32, PUM_ERR_INVALID_ARG, "smooth_dt must be F64 or F32");
   PUM_CHECK(sp->g_dt == PUM_F64 || sp->g_dt == PUM_F32 || sp->g_dt == PUM_BF16, PUM_ERR_INVALID_ARG, "g_dt");
@@ -205,7 +221,7 @@ const Bsr* select_matrix(const pum_hier* h, int level, int which) {
 
 // ---- persistence helpers
 const uint32_t kMagic = 0x484D5550u;  // "PUMH"
-const uint32_t kVersion = 1;
+const uint32_t kVersion = 2;
 
 void wr(FILE* f, const void* p, size_t n) {
   PUM_CHECK(n == 0 || fwrite(p, 1, n, f) == n, PUM_ERR_IO, "write failed");
@@ -410,6 +426,8 @@ pum_status bfsai_setup(pum_ctx* ctx, pum_hier* h, const bfsai_params* fp, const 
     h->sell = ctx->sell;
     const int nl = (int)h->lv.size();
     PUM_CHECK(h->lv.back().n * h->lv.back().d <= 4096, PUM_ERR_UNSUPPORTED, "coarsest level above 4096 unknowns");
+    PUM_CHECK(sp->smooth_dt == PUM_F64 || sp->fp32_levels >= nl || sp->fp32_levels <= sp->mixed_levels,
+              PUM_ERR_INVALID_ARG, "fp32_levels below the level count needs fp32_levels <= mixed_levels");
     for (int l = 0; l + 1 < nl; ++l) {
       try {
         fsai_setup_level(ctx, h, l);
@@ -434,10 +452,10 @@ pum_status cheb4_smooth(pum_ctx* ctx, pum_hier* h, int level, const double* b, d
     check_vec(x, "x");
     Level& L = h->lv[level];
     const int64_t N = (int64_t)L.n * L.d;
-    convert_vec(ctx, L.b, h->smooth_dt, b, PUM_F64, N);
-    if (!x_is_zero) convert_vec(ctx, L.x, h->smooth_dt, x, PUM_F64, N);
+    convert_vec(ctx, L.b, L.vdt, b, PUM_F64, N);
+    if (!x_is_zero) convert_vec(ctx, L.x, L.vdt, x, PUM_F64, N);
     cheb4(ctx, h, level, L.b, L.x, x_is_zero != 0, nullptr, -1, false);
-    convert_vec(ctx, x, PUM_F64, L.x, h->smooth_dt, N);
+    convert_vec(ctx, x, PUM_F64, L.x, L.vdt, N);
     return PUM_OK;
   });
 }
@@ -492,9 +510,9 @@ pum_status pum_fsai_apply(pum_ctx* ctx, pum_hier* h, int level, const double* r,
     check_vec(z, "z");
     Level& L = h->lv[level];
     const int64_t N = (int64_t)L.n * L.d;
-    convert_vec(ctx, L.r, h->smooth_dt, r, PUM_F64, N);
+    convert_vec(ctx, L.r, L.vdt, r, PUM_F64, N);
     apply_M(ctx, h, level, L.r, L.p, -1);
-    convert_vec(ctx, z, PUM_F64, L.p, h->smooth_dt, N);
+    convert_vec(ctx, z, PUM_F64, L.p, L.vdt, N);
     return PUM_OK;
   });
 }

@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(256) k_bsr_mv(int n_brows, int stride, int lan
 constexpr unsigned kAllEpi = 0x7Fu;
 constexpr unsigned kResidOnly = 1u << EPI_RESID;
 constexpr unsigned kAddOnly = 1u << EPI_ADD;
+constexpr unsigned kSetOnly = 1u << EPI_SET;
 constexpr unsigned kChebOnly = (1u << EPI_CHEB_FIRST0) | (1u << EPI_CHEB_FIRST) | (1u << EPI_CHEB);
 
 template <int D, typename MT, typename XT, typename YT, typename X2T, unsigned EPIS>
@@ -145,6 +146,9 @@ static void launch_mv_d(pum_ctx* ctx, const Bsr& M, int vdt, const void* x, int 
   // FP32 prolongation added into an FP64 iterate
   if (mdt == PUM_F32 && xdt == PUM_F32 && ydt == PUM_F64)
     return launch_mv_epi<D, float, float, double, double, kAddOnly>(ctx, M, x, epi, e);
+  // FP64 restriction of an FP32 residual to a level that smooths in FP64
+  if (mdt == PUM_F64 && xdt == PUM_F32 && ydt == PUM_F64)
+    return launch_mv_epi<D, double, float, double, double, kSetOnly>(ctx, M, x, epi, e);
   throw Error{PUM_ERR_UNSUPPORTED, "bsr_mv: unsupported matrix/vector precision mix"};
 }
 

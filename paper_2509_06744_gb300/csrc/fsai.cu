@@ -687,10 +687,11 @@ void lanczos_level(pum_ctx* ctx, pum_hier* h, int l) {
   Bsr G, GT, F0, F0T;
   const bool nested = h->fp.nested;
   // FP64 copy of a factor rounded through the smoother's storage precision
+  const int gdt = level_gdt(h, l);
   auto rounded = [&](Bsr& dst, const Bsr& src64) {
-    if (h->g_dt == PUM_F64) { bsr_convert(dst, src64, PUM_F64, s); return; }
+    if (gdt == PUM_F64) { bsr_convert(dst, src64, PUM_F64, s); return; }
     Bsr tmp;
-    bsr_convert(tmp, src64, h->g_dt, s);
+    bsr_convert(tmp, src64, gdt, s);
     bsr_widen(dst, tmp, s);
     bsr_free(tmp);
   };

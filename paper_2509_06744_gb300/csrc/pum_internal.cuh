@@ -93,6 +93,10 @@ void bsr_free(Bsr& m);
 void sell_build(Bsr& m, cudaStream_t s, int sm_count);
 void sell_free(Sell& s);
 bool sell_mv(pum_ctx* ctx, const Bsr& M, int vdt, const void* x, int epi, const struct EpiArgs& e);
+// Smoother precision of level l (FP32 only on the first fp32_levels levels of the FP32 form)
+// and the precision its FSAI factors are stored in.
+int level_vdt(const pum_hier* h, int l);
+int level_gdt(const pum_hier* h, int l);
 // Sliced layout of an FP64 matrix as FP32 pairs (hi = fl32(a), lo = fl32(a - hi)), and its
 // product with a split vector (float2 hi, lo per unknown) in double-float arithmetic: RESID
 // into an FP32 y with an FP64 b, or ADD into an FP64 y.
@@ -125,6 +129,7 @@ void spgemm(Bsr& C, const Bsr& X, const Bsr& Y, cudaStream_t s);
 
 struct Level {
   int m = 0, n = 0, d = 0;
+  int vdt = PUM_F64, gdt = PUM_F64;  // this level's smoother storage/arithmetic and G precision
   Bsr A;                // FP64 operator
   Bsr As;               // smoothing copy (F32) when smooth_dt == F32
   Bsr P, PT;            // FP64 prolongation from level+1 and its transpose
@@ -145,6 +150,7 @@ struct Level {
   // the split (hi, lo) shadow of the level's FP64 iterate that those products read.
   Sell Adf;
   void* zs = nullptr;
+  Sell Pdf;  // P as FP32 pairs, when the coarser level is a mixed sliced level too
 };
 
 struct Coarse {

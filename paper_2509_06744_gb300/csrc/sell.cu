@@ -28,8 +28,8 @@ namespace pum {
 namespace {
 
 constexpr int kWaitLimit = 1 << 22;  // polls of an mbarrier before a wait gives up
-constexpr int kHeader = 128;         // bytes for up to 8 full/empty barrier pairs
-constexpr int kMaxStages = 4;
+constexpr int kHeader = 128;         // bytes for the full/empty barriers of up to 8 stages
+constexpr int kMaxStages = 8;
 constexpr int kSellMaxThreads = 32 + 352;  // producer warp + the largest consumer group (d = 21, R = 16)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -213,7 +213,8 @@ __global__ void __launch_bounds__(kSellMaxThreads) k_sell_mv(int n_brows, int R,
   }
 }
 
-// Ring depth: as many stages as fit in about 40 KB, between 2 and 4.
+// Ring depth: as many stages as fit in about 40 KB, between 2 and 8 (small chunks of small
+// groups need more of them in flight per CTA).
 static int sell_stages(size_t chunk) { return (int)std::max<size_t>(2, std::min<size_t>(kMaxStages, 40960 / chunk)); }
 
 static size_t sell_smem(const Sell& S, int d, size_t vsize) {

@@ -43,12 +43,12 @@ void timing_end(pum_ctx* ctx, int tk) {
 
 // ----------------------------------------------------------------------------- smoother
 
-static const Bsr& smoothA(pum_hier* h, int l) { return h->smooth_dt == PUM_F64 ? h->lv[l].A : h->lv[l].As; }
+static const Bsr& smoothA(pum_hier* h, int l) { return h->lv[l].vdt == PUM_F64 ? h->lv[l].A : h->lv[l].As; }
 
 // z = M r with the level's block-FSAI factors; the last product carries the epilogue.
 static void fsai_apply_epi(pum_ctx* ctx, pum_hier* h, int l, const void* r, int epi, EpiArgs e) {
   Level& L = h->lv[l];
-  const int vdt = h->smooth_dt;
+  const int vdt = L.vdt;
   const bool fin = (l == 0);
   EpiArgs s{};
   if (!h->fp.nested) {
@@ -77,7 +77,7 @@ void apply_M(pum_ctx* ctx, pum_hier* h, int l, const void* r, void* z, int) {
 void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_zero, void* x_acc, int acc_dt,
            bool acc_set, void* x_acc_split) {
   Level& L = h->lv[l];
-  const int vdt = h->smooth_dt;
+  const int vdt = L.vdt;
   const int k = h->sp.degree_k;
   const double dd = 4.0 / L.beta;  // d = 4 / beta
   const bool fin = (l == 0);
@@ -157,7 +157,7 @@ void coarse_solve(pum_ctx* ctx, pum_hier* h, const void* b, void* x, int vdt) {
 // formed the same way.  In exact arithmetic this is the same cycle.
 void vcycle_level(pum_ctx* ctx, pum_hier* h, int l) {
   Level& L = h->lv[l];
-  const int vdt = h->smooth_dt;
+  const int vdt = L.vdt;
   if (l == (int)h->lv.size() - 1) {
     coarse_solve(ctx, h, L.b, L.x, vdt);
     return;
@@ -264,7 +264,7 @@ static bool capturable(pum_ctx* ctx) {
 // operator on the FP64 z and r; the coarse correction of a mixed coarser level is
 // prolongated with the FP64 P.  In exact arithmetic this is the same V(k,k) cycle.
 static bool is_mixed(const pum_hier* h, int l) {
-  return h->smooth_dt == PUM_F32 && l < h->sp.mixed_levels;
+  return h->lv[l].vdt == PUM_F32 && l < h->sp.mixed_levels;
 }
 
 // y = b - A z with FP64 b and z, FP32 y, to FP64 accuracy: on the sliced layout in double-float
@@ -297,16 +297,27 @@ static void vcycle_mixed(pum_ctx* ctx, pum_hier* h, int l, const double* r, doub
   accurate_residual(ctx, L, z, er, tk);  // r_f = r - A z
   EpiArgs rs{};
   rs.y = C.b;
-  bsr_mv(ctx, L.PTs, PUM_F32, L.r, EPI_SET, rs);  // b_c = P^T r_f
   EpiArgs pa{};
-  if (is_mixed(h, l + 1) || l + 1 == (int)h->lv.size() - 1) {
+  if (C.vdt == PUM_F64) {  // the coarser levels smooth in FP64: an FP64 cycle from there down
+    rs.xdt = PUM_F32;
+    bsr_mv(ctx, L.PT, PUM_F64, L.r, EPI_SET, rs);  // b_c = P^T r_f (FP64)
+    vcycle_level(ctx, h, l + 1);
+    pa.y = z;
+    pa.ys = L.zs;
+    bsr_mv(ctx, L.P, PUM_F64, C.x, EPI_ADD, pa);  // z += P x_c (FP64)
+  } else if (is_mixed(h, l + 1) || l + 1 == (int)h->lv.size() - 1) {
+    bsr_mv(ctx, L.PTs, PUM_F32, L.r, EPI_SET, rs);  // b_c = P^T r_f
     const int64_t Nc = (int64_t)C.n * C.d;
     convert_vec(ctx, C.b64, PUM_F64, C.b, PUM_F32, Nc);
     vcycle_mixed(ctx, h, l + 1, C.b64, C.z64);
     pa.y = z;
     pa.ys = L.zs;
-    bsr_mv(ctx, L.P, PUM_F64, C.z64, EPI_ADD, pa);  // z += P z_c (FP64)
+    if (L.Pdf.R)
+      sell_df_mv(ctx, L.Pdf, L.d, L.n, C.zs, EPI_ADD, pa);  // z += P z_c in double-float arithmetic
+    else
+      bsr_mv(ctx, L.P, PUM_F64, C.z64, EPI_ADD, pa);  // z += P z_c (FP64)
   } else {
+    bsr_mv(ctx, L.PTs, PUM_F32, L.r, EPI_SET, rs);  // b_c = P^T r_f
     vcycle_level(ctx, h, l + 1);
     pa.y = z;
     pa.ys = L.zs;
@@ -319,7 +330,7 @@ static void vcycle_mixed(pum_ctx* ctx, pum_hier* h, int l, const double* r, doub
   cr.xdt = PUM_F64;
   cr.ydt = PUM_F32;
   accurate_residual(ctx, L, z, cr, tk);                 // c = r - A z
-  cheb4(ctx, h, l, L.c, L.e, true, z, PUM_F64, false);  // A e = c from 0; z += updates
+  cheb4(ctx, h, l, L.c, L.e, true, z, PUM_F64, false, L.zs);  // A e = c from 0; z += updates
 }
 
 static void vcycle_body(pum_ctx* ctx, pum_hier* h, const double* r, double* z) {
@@ -329,9 +340,9 @@ static void vcycle_body(pum_ctx* ctx, pum_hier* h, const double* r, double* z) {
     vcycle_mixed(ctx, h, 0, r, z);
     return;
   }
-  convert_vec(ctx, L0.b, h->smooth_dt, r, PUM_F64, N);
+  convert_vec(ctx, L0.b, L0.vdt, r, PUM_F64, N);
   vcycle_level(ctx, h, 0);
-  convert_vec(ctx, z, PUM_F64, L0.x, h->smooth_dt, N);
+  convert_vec(ctx, z, PUM_F64, L0.x, L0.vdt, N);
 }
 
 static void build_vcycle_graph(pum_ctx* ctx, pum_hier* h, const double* r, double* z) {

@@ -76,6 +76,7 @@ class Problem:
     cheb_k: int
     smooth_dtype: str        # "f64", "f32"
     g_dtype: str             # "f64", "f32", "bf16"
+    fp32_levels: int = 64    # FP32 form: levels smoothed in FP32 (the coarser ones in FP64)
 
     @property
     def nitsche(self) -> tuple:
@@ -101,7 +102,7 @@ SMALL_BIHARMONIC = Problem("biharmonic p=3 16x16 patches, 4 levels, static block
 BIHARMONIC_256 = Problem("biharmonic p=3 256x256 patches, 9 levels, adaptive block-FSAI t_max=6, Chebyshev-4 k=3",
                          4, 3, 256, 9, 1, 2.0, "lower", True, 6, 1.0, False, 3, "f64", "f64")
 TRIHARMONIC_256 = Problem("triharmonic p=5 256x256 patches, 9 levels, nested adaptive block-FSAI, Chebyshev-4 k=4",
-                          6, 5, 256, 9, 2, 3.0, "diag", True, 6, 1.0, True, 4, "f32", "bf16")
+                          6, 5, 256, 9, 2, 3.0, "diag", True, 6, 1.0, True, 4, "f32", "bf16", 2)
 
 
 def splitmix64_reference_values():

@@ -281,14 +281,14 @@ def test_fp32_smoothing_fp64_outer_reaches_tolerance(lib, ctx, small_biharmonic,
 
 
 def test_fp32_form_double_float_residuals(lib):
-    """64x64 patches: the finest level (4096 block rows) is on the sliced layout, so the FP32
-    form's two accurate residuals per cycle run in double-float arithmetic there.  The solve
-    must match the plain FP64 form (iterations, history, solution) as closely as the same FP32
-    form with FP64-operator residuals (sliced layout off) does."""
+    """128x128 patches: the two finest levels (16384 and 4096 block rows) are on the sliced
+    layout, so the FP32 form's accurate residuals on both, and the prolongation between them,
+    run in double-float arithmetic.  The solve must match the plain FP64 form (iterations,
+    history, solution) as closely as the same FP32 form with FP64 products (sliced layout off)."""
     import os
     import torch
     pr = pin.SMALL_BIHARMONIC
-    m, levels = 64, 7
+    m, levels = 128, 8
     out = {}
     for form in ("f64", "df", "fp64op"):
         if form == "fp64op":
@@ -314,6 +314,41 @@ def test_fp32_form_double_float_residuals(lib):
         h, h64 = np.array(out[form][0]["history"]), np.array(out["f64"][0]["history"])
         assert np.max(np.abs(h - h64) / h64) <= 1e-2  # FP32 smoothing perturbs each cycle slightly
         assert norm_rel(out[form][1], out["f64"][1]) <= 1e-7
+
+
+def test_fp32_levels_switch_coarse_levels_to_fp64(lib, ctx, small_biharmonic):
+    """fp32_levels: FP32 smoothing on the finest levels only.  With 0 FP32 levels the cycle is
+    the FP64 cycle bit for bit; with 1 the solve matches the FP64 form; a switch below the
+    mixed levels is rejected."""
+    import torch
+    h = small_biharmonic
+    H = hier_from_oracle(lib, ctx, h)
+    r = cuda(pin.normal_vector(PR.n_dofs, 31))
+    H.setup(p0="lower", k=PR.cheb_k)
+    z64 = torch.zeros_like(r)
+    H.vcycle(r, z64)
+    H.setup(p0="lower", k=PR.cheb_k, smooth="f32", g="f32", fp32_levels=0)
+    z0 = torch.zeros_like(r)
+    H.vcycle(r, z0)
+    assert np.array_equal(host(z0), host(z64))
+    H.setup(p0="lower", k=PR.cheb_k, smooth="f32", g="bf16", fp32_levels=1)
+    assert [H.info(l)["beta"] for l in range(1, PR.n_levels - 1)] == \
+        [b for b in _betas_fp64(lib, ctx, h)[1:]]  # coarse levels keep FP64 factors
+    x = torch.zeros_like(r)
+    rep = H.pcg(cuda(h.b), x, rtol=1e-8, maxit=100, flexible=True)
+    ref = solver.solve(solver.build_setup(h, k=PR.cheb_k, mode="static", P0="lower"), h.b, rtol=1e-10)
+    assert rep["converged"] and norm_rel(host(x), ref.x) <= 1e-5
+    with pytest.raises(lib.PumError):
+        H.setup(p0="lower", k=PR.cheb_k, smooth="f32", g="f32", mixed_levels=1, fp32_levels=2)
+    H.close()
+
+
+def _betas_fp64(lib, ctx, h):
+    H = hier_from_oracle(lib, ctx, h)
+    H.setup(p0="lower", k=PR.cheb_k)
+    b = [H.info(l)["beta"] for l in range(PR.n_levels - 1)]
+    H.close()
+    return b
 
 
 def test_save_load_roundtrip_bitwise(lib, ctx, static_pair, tmp_path):
