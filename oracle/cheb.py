@@ -5,6 +5,8 @@ Test infrastructure only (never imported by the CUDA library).
 * ``cheb4``: Algorithm 3 step by step: r = b - A x0, p = M r, mu = 1/3, d = 4/beta,
   x = x0 + d mu p; then for i = 2..k: r = b - A x, p = mu^2 p + M r, mu = 1/(2 - mu),
   x = x + d mu p.  The residual is recomputed from b - A x in every iteration.
+* ``richardson``: Richardson smoothing (Section 3.1), k steps of x = x + M (b - A x),
+  so the error propagates by S = (I - M A)^k.
 * ``w4``: W_k, the Chebyshev polynomial of the fourth kind, by its three-term
   recurrence W_0 = 1, W_1 = 2t + 1, W_{n+1} = 2t W_n - W_{n-1} (Section 3.1);
   the optimal smoother polynomial of Eq. (3.6) is W_k(1 - 2 lambda / beta) / (2k + 1).
@@ -35,6 +37,14 @@ def cheb4(Aop, Mop, b: np.ndarray, x0: np.ndarray | None, beta: float, k: int) -
         p = mu * mu * p + Mop(r)
         mu = 1.0 / (2.0 - mu)
         x = x + d * mu * p
+    return x
+
+
+def richardson(Aop, Mop, b: np.ndarray, x0: np.ndarray | None, k: int) -> np.ndarray:
+    """Richardson smoothing (Section 3.1): k repeated applications of the preconditioner."""
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    for _i in range(k):
+        x = x + Mop(b - Aop(x))
     return x
 
 

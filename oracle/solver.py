@@ -13,6 +13,11 @@ Test infrastructure only (never imported by the CUDA library).
   as the Krylov method for the symmetric cycle (Conclusions).
 * ``convergence_factor``: rho_A of Example 5.1 for the stationary cycle run on the
   error equation (b = 0), e_n = (I - B A) e_{n-1}.
+* Variants of Section 5: Richardson smoothing instead of Algorithm 3 (``smoother =
+  "richardson"``), and the non-symmetric V(2k,0) cycle (``cycle = "v2k0"``: 2k steps of
+  pre-smoothing, none after the coarse correction), which cannot precondition CG; the
+  Conclusions name BiCGStab for it: ``bicgstab`` is van der Vorst's (1992) BiCGStab with the
+  cycle as right preconditioner.
 """
 from __future__ import annotations
 
@@ -38,6 +43,8 @@ class Level:
 class Setup:
     levels: list
     k: int
+    smoother: str = "cheb4"   # "cheb4" (Algorithm 3) or "richardson"
+    cycle: str = "vkk"        # "vkk": V(k,k); "v2k0": V(2k,0)
 
 
 def make_smoother(A: bk.BlockCSR, mode: str, P0: str, t_max: int, tau: float, nested: bool,
@@ -84,18 +91,25 @@ def _symmetric_form(obj, nested):
     return op
 
 
+def _smooth(setup: Setup, lev: Level, b: np.ndarray, x0, steps: int) -> np.ndarray:
+    if setup.smoother == "richardson":
+        return cheb.richardson(lev.A.matvec, lev.M, b, x0, steps)
+    return cheb.cheb4(lev.A.matvec, lev.M, b, x0, lev.beta, steps)
+
+
 def vcycle(setup: Setup, r: np.ndarray, l: int = 0) -> np.ndarray:
-    """z = B r, one V(k,k) cycle started on level l."""
+    """z = B r, one V(k,k) (or V(2k,0)) cycle started on level l."""
     lev = setup.levels[l]
     if lev.chol is not None:
         return sla.cho_solve((lev.chol, True), r)
-    Aop = lev.A.matvec
-    x = cheb.cheb4(Aop, lev.M, r, None, lev.beta, setup.k)
-    res = r - Aop(x)
+    pre = setup.k if setup.cycle == "vkk" else 2 * setup.k
+    x = _smooth(setup, lev, r, None, pre)
+    res = r - lev.A.matvec(x)
     rc = lev.P.to_scipy().T @ res
     ec = vcycle(setup, rc, l + 1)
     x = x + lev.P.matvec(ec)
-    x = cheb.cheb4(Aop, lev.M, r, x, lev.beta, setup.k)
+    if setup.cycle == "vkk":
+        x = _smooth(setup, lev, r, x, setup.k)
     return x
 
 
@@ -131,6 +145,49 @@ def pcg(Aop, Bop, b: np.ndarray, rtol: float = 1e-8, maxit: int = 500) -> PCGRes
         p = z + (rz_new / rz) * p
         rz = rz_new
     return PCGResult(x, hist, maxit, False)
+
+
+def bicgstab(Aop, Bop, b: np.ndarray, rtol: float = 1e-8, maxit: int = 500) -> PCGResult:
+    """BiCGStab (van der Vorst 1992) from x0 = 0 with B as right preconditioner; the shadow
+    residual is r0 = b.  history holds ||r_j|| / ||b|| after each full step (the stop test);
+    a half step whose s already meets rtol ends the iteration there."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    rhat = b.copy()
+    nb = float(np.linalg.norm(b))
+    hist = [1.0]
+    if nb == 0.0:
+        return PCGResult(x, hist, 0, True)
+    rho_old = alpha = omega = 1.0
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    for it in range(1, maxit + 1):
+        rho = float(rhat @ r)
+        beta = (rho / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        ph = Bop(p)
+        v = Aop(ph)
+        alpha = rho / float(rhat @ v)
+        s = r - alpha * v
+        if float(np.linalg.norm(s)) / nb <= rtol:
+            x = x + alpha * ph
+            hist.append(float(np.linalg.norm(s)) / nb)
+            return PCGResult(x, hist, it, True)
+        sh = Bop(s)
+        t = Aop(sh)
+        omega = float(t @ s) / float(t @ t)
+        x = x + alpha * ph + omega * sh
+        r = s - omega * t
+        hist.append(float(np.linalg.norm(r)) / nb)
+        if hist[-1] <= rtol:
+            return PCGResult(x, hist, it, True)
+        rho_old = rho
+    return PCGResult(x, hist, maxit, False)
+
+
+def solve_bicgstab(setup: Setup, b: np.ndarray, rtol: float = 1e-8, maxit: int = 500) -> PCGResult:
+    A = setup.levels[0].A
+    return bicgstab(A.matvec, lambda r: vcycle(setup, r), b, rtol, maxit)
 
 
 def solve(setup: Setup, b: np.ndarray, rtol: float = 1e-8, maxit: int = 500) -> PCGResult:
