@@ -199,6 +199,34 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measure_variants(H, pr, b, stream, steps):
+    """The paper's cycle/smoother comparisons on the same workload (FP32 form): the V(2k,0)
+    cycle under BiCGStab (time to 1e-8) and the convergence factor rho_A of the stationary
+    V(k,k), V(2k,0) and Richardson-smoothed V(k,k) cycles (6 cycles from a U(-1,1) error)."""
+    import torch
+    kw = dict(p0=pr.fsai_p0, adaptive=pr.adaptive, t_max=pr.t_max, tau=pr.tau, k=pr.cheb_k, smooth="f32", g="f32")
+    e0 = torch.tensor(pin.uniform_vector(pr.n_dofs, 5), dtype=torch.float64, device="cuda")
+    out = {"rho_A": {}}
+    for name, extra in (("v2k0", dict(cycle="v2k0")), ("richardson_vkk", dict(smoother="richardson")),
+                        ("vkk", {})):
+        H.setup(**kw, **extra)
+        out["rho_A"][name] = H.convergence_factor(e0, 6)
+        if name == "v2k0":
+            x = torch.zeros_like(b)
+            for _ in range(2):
+                H.bicgstab(b, x, rtol=RTOL, maxit=200)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(steps):
+                rep = H.bicgstab(b, x, rtol=RTOL, maxit=200)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            out["v2k0_bicgstab"] = {"ms_per_solve": ev0.elapsed_time(ev1) / steps, "iters": rep["iters"],
+                                    "cycles_per_solve": 2 * rep["iters"], "solves": steps}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -206,6 +234,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the V(2k,0) / Richardson measurements")
     ap.add_argument("--profile", action="store_true",
                     help="FP32 form only: one solve bracketed by cudaProfilerStart/Stop (for ncu "
                          "--profile-from-start off); prints the launch count")
@@ -343,6 +372,7 @@ def main():
                    "GBps": (ab[k] / (v[1] / v[0] * 1e-3) / 1e9) if v[0] else None,
                    "total_ms_per_solve": v[1] / args.steps} for k, v in kt.items()}
     dom = max(("resid", "g", "gt", "resid64"), key=lambda k: kt[k][1])
+    variants = measure_variants(H, pr, b, stream, max(3, args.steps // 4)) if not args.no_variants else None
 
     if rank != 0:
         return
@@ -371,6 +401,7 @@ def main():
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

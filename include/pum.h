@@ -97,6 +97,15 @@ typedef struct {
   double tie_rel;   /* argmin ties: smallest column with rho_c <= rho_min (1 + tie_rel)    */
 } bfsai_params;
 
+/* Smoother and cycle variants of Section 5 (the paper's comparisons). */
+enum { PUM_SMOOTHER_CHEB4 = 0,      /* Algorithm 3, fourth-kind Chebyshev of degree k            */
+       PUM_SMOOTHER_RICHARDSON = 1  /* k steps x <- x + M (b - A x): S = (I - M A)^k (Section 3.1) */
+};
+enum { PUM_CYCLE_VKK = 0,   /* V(k,k): the same smoother before and after (symmetric: CG)         */
+       PUM_CYCLE_V2K0 = 1   /* V(2k,0): 2k steps before the coarse correction, none after
+                               (non-symmetric: bicgstab_solve, not pcg_solve)                      */
+};
+
 /* Fourth-kind Chebyshev smoother (Algorithm 3) and its lambda_max estimate (Section 5). */
 typedef struct {
   int32_t degree_k;      /* k >= 1 smoothing steps, pre and post (V(k,k))                  */
@@ -116,6 +125,8 @@ typedef struct {
                             numbers near 1/eps_32).  A level count below n_levels needs
                             fp32_levels <= mixed_levels (the switch happens under a mixed
                             level); >= n_levels: every level                                   */
+  int32_t smoother;      /* PUM_SMOOTHER_CHEB4 or PUM_SMOOTHER_RICHARDSON                     */
+  int32_t cycle;         /* PUM_CYCLE_VKK or PUM_CYCLE_V2K0                                   */
 } smoother_params;
 
 /* Outer preconditioned CG (one V(k,k) cycle as preconditioner). */
@@ -198,6 +209,20 @@ pum_status vcycle_apply(pum_ctx *ctx, pum_hier *h, const double *r, double *z);
  * A_0 q products in float64).  b, x: device float64, N_finest.  Synchronous; fills rep.
  * Returns PUM_ERR_NOCONV when maxit is reached (x holds the last iterate). */
 pum_status pcg_solve(pum_ctx *ctx, pum_hier *h, const double *b, double *x, pcg_report *rep);
+
+/* BiCGStab (van der Vorst 1992) from x = 0 with one cycle as right preconditioner, the Krylov
+ * method the Conclusions name for the non-symmetric V(2k,0) cycle (any cycle is accepted).
+ * Shadow residual r^ = b.  float64 vectors and A_0 products; b, x: device float64, N_finest.
+ * rep->hist gets ||r_j|| / ||b|| after each iteration (2 cycles and 2 products); rep->flexible
+ * is ignored.  Synchronous; PUM_ERR_BREAKDOWN when r^.r, r^.v or t.t vanishes, PUM_ERR_NOCONV
+ * at maxit (x holds the last iterate).  Work vectors are allocated on the first call. */
+pum_status bicgstab_solve(pum_ctx *ctx, pum_hier *h, const double *b, double *x, pcg_report *rep);
+
+/* Convergence factor rho_A of the stationary cycle (the measure of the paper's Section 5
+ * figures): e_j = (I - B A) e_{j-1} for j = 1..n_cycles from the caller's e0 (device float64,
+ * N_finest, not modified), rho = (e_n^T A e_n / e_0^T A e_0)^(1 / (2 n_cycles)).  *rho is a host
+ * double.  Synchronous. */
+pum_status pum_convergence_factor(pum_ctx *ctx, pum_hier *h, const double *e0, int n_cycles, double *rho);
 
 /* ---- single steps of the hot path (device float64 vectors) ------------------------ */
 

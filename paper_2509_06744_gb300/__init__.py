@@ -20,6 +20,8 @@ __all__ = ["Context", "Hierarchy", "PumError", "PUM_F64", "PUM_F32", "PUM_BF16",
            "PUM_MAT_A", "PUM_MAT_P", "PUM_MAT_G", "PUM_MAT_GT", "PUM_MAT_F0", "PUM_MAT_G1", "PUM_MAT_A1"]
 
 _DT = {"f64": PUM_F64, "f32": PUM_F32, "bf16": PUM_BF16}
+_SMOOTHER = {"cheb4": 0, "richardson": 1}   # PUM_SMOOTHER_*
+_CYCLE = {"vkk": 0, "v2k0": 1}             # PUM_CYCLE_*
 
 
 class PumError(RuntimeError):
@@ -171,11 +173,11 @@ class Hierarchy:
     def setup(self, p0: str = "lower", adaptive: bool = False, t_max: int = 0, tau: float = 1.0,
               nested: bool = False, tie_rel: float = 1e-9, k: int = 2, lanczos_its: int = 100,
               lanczos_safety: float = 1.01, lanczos_seed: int = 0, smooth: str = "f64", g: str | None = None,
-              mixed_levels: int = 64, fp32_levels: int = 64):
+              mixed_levels: int = 64, fp32_levels: int = 64, smoother: str = "cheb4", cycle: str = "vkk"):
         fp = _lib.FsaiParams(PUM_P0_LOWER if p0 == "lower" else PUM_P0_DIAG, int(adaptive), t_max, tau,
                              int(nested), tie_rel)
         sp = _lib.SmootherParams(k, lanczos_its, lanczos_safety, lanczos_seed, _DT[smooth], _DT[g or smooth],
-                                 int(mixed_levels), int(fp32_levels))
+                                 int(mixed_levels), int(fp32_levels), _SMOOTHER[smoother], _CYCLE[cycle])
         self.ctx.check(self.lib.bfsai_setup(self.ctx.h, self.h, C.byref(fp), C.byref(sp)))
 
     def close(self):
@@ -197,13 +199,27 @@ class Hierarchy:
         self.ctx.check(self.lib.vcycle_apply(self.ctx.h, self.h, _vec(r, "r"), _vec(z, "z")))
 
     def pcg(self, b, x, rtol: float = 1e-8, maxit: int = 200, flexible: bool = False, allow_noconv=False):
+        return self._krylov(self.lib.pcg_solve, b, x, rtol, maxit, flexible, allow_noconv)
+
+    def bicgstab(self, b, x, rtol: float = 1e-8, maxit: int = 200, allow_noconv=False):
+        """BiCGStab with the cycle as right preconditioner (for the non-symmetric V(2k,0))."""
+        return self._krylov(self.lib.bicgstab_solve, b, x, rtol, maxit, False, allow_noconv)
+
+    def _krylov(self, fn, b, x, rtol, maxit, flexible, allow_noconv):
         hist = (C.c_double * (maxit + 1))()
         rep = _lib.PcgReport(rtol, maxit, int(flexible), hist, 0, 0, 0.0)
-        st = self.lib.pcg_solve(self.ctx.h, self.h, _vec(b, "b"), _vec(x, "x"), C.byref(rep))
+        st = fn(self.ctx.h, self.h, _vec(b, "b"), _vec(x, "x"), C.byref(rep))
         if not (st == 0 or (allow_noconv and st == _lib.PUM_ERR_NOCONV)):
             self.ctx.check(st)
         return {"iters": rep.iters, "converged": bool(rep.converged), "final_relres": rep.final_relres,
                 "history": [hist[i] for i in range(rep.iters + 1)]}
+
+    def convergence_factor(self, e0, n_cycles: int) -> float:
+        """rho_A of the stationary cycle from the error e0 (the measure of the paper's figures)."""
+        rho = C.c_double(0.0)
+        self.ctx.check(self.lib.pum_convergence_factor(self.ctx.h, self.h, _vec(e0, "e0"), int(n_cycles),
+                                                       C.byref(rho)))
+        return rho.value
 
     # ---- single steps
     def residual(self, level, b, x, r):

@@ -43,7 +43,7 @@ class FsaiParams(C.Structure):
 class SmootherParams(C.Structure):
     _fields_ = [("degree_k", c_int32), ("lanczos_its", c_int32), ("lanczos_safety", c_double),
                 ("lanczos_seed", C.c_uint64), ("smooth_dt", c_int32), ("g_dt", c_int32), ("mixed_levels", c_int32),
-                ("fp32_levels", c_int32)]
+                ("fp32_levels", c_int32), ("smoother", c_int32), ("cycle", c_int32)]
 
 
 class PcgReport(C.Structure):
@@ -69,6 +69,8 @@ _SIGNATURES = {
     "cheb4_smooth": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_int32]),
     "vcycle_apply": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "pcg_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, P(PcgReport)]),
+    "bicgstab_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, P(PcgReport)]),
+    "pum_convergence_factor": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, P(c_double)]),
     "pum_residual": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "pum_fsai_apply": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "pum_restrict": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),

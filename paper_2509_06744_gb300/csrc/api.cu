@@ -12,6 +12,8 @@
 namespace pum {
 void vcycle_apply_impl(pum_ctx* ctx, pum_hier* h, const double* r, double* z);
 pum_status pcg_impl(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_report* rep);
+pum_status bicgstab_impl(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_report* rep);
+double convergence_factor_impl(pum_ctx* ctx, pum_hier* h, const double* e0, int n_cycles);
 }  // namespace pum
 
 using namespace pum;
@@ -81,6 +83,8 @@ void free_smoother(pum_hier* h) {
     sell_free(L.Pdf);
   }
   for (auto& w : h->w64)
+    if (w) { cudaFree(w); w = nullptr; }
+  for (auto& w : h->wb)
     if (w) { cudaFree(w); w = nullptr; }
   h->setup_done = false;
 }
@@ -178,9 +182,10 @@ void finalize_smoother(pum_ctx* ctx, pum_hier* h) {
   }
   const size_t N0 = (size_t)h->lv[0].n * h->lv[0].d;
   for (auto& w : h->w64) w = (double*)dalloc(sizeof(double) * N0);
-  h->mu.assign(h->sp.degree_k, 0.0);
-  double mu = 1.0 / 3.0;  // Algorithm 3: mu_1 = 1/3, mu_{i+1} = 1 / (2 - mu_i)
-  for (int i = 0; i < h->sp.degree_k; ++i) {
+  const int steps = h->sp.cycle == PUM_CYCLE_V2K0 ? 2 * h->sp.degree_k : h->sp.degree_k;
+  h->mu.assign(steps, 0.0);
+  double mu = 1.0 / 3.0;  // Algorithm 3: mu_1 = 1/3, mu_{i+1} = 1 / (2 - mu_i), whatever the degree
+  for (int i = 0; i < steps; ++i) {
     h->mu[i] = mu;
     mu = 1.0 / (2.0 - mu);
   }
@@ -197,6 +202,10 @@ void check_params(const bfsai_params* fp, const smoother_params* sp) {
   PUM_CHECK(sp->degree_k >= 1 && sp->degree_k <= 64, PUM_ERR_INVALID_ARG, "degree_k must be in 1..64");
   PUM_CHECK(sp->lanczos_its >= 1 && sp->lanczos_safety >= 1.0, PUM_ERR_INVALID_ARG, "Lanczos parameters");
   PUM_CHECK(sp->fp32_levels >= 0, PUM_ERR_INVALID_ARG, "fp32_levels must be >= 0");
+  PUM_CHECK(sp->smoother == PUM_SMOOTHER_CHEB4 || sp->smoother == PUM_SMOOTHER_RICHARDSON, PUM_ERR_INVALID_ARG,
+            "smoother must be PUM_SMOOTHER_CHEB4 or PUM_SMOOTHER_RICHARDSON");
+  PUM_CHECK(sp->cycle == PUM_CYCLE_VKK || sp->cycle == PUM_CYCLE_V2K0, PUM_ERR_INVALID_ARG,
+            "cycle must be PUM_CYCLE_VKK or PUM_CYCLE_V2K0");
   PUM_CHECK(sp->mixed_levels >= 0, PUM_ERR_INVALID_ARG, "mixed_levels must be >= 0");
   PUM_CHECK(sp->smooth_dt == PUM_F64 || sp->smooth_dt == PUM_F32, PUM_ERR_INVALID_ARG, "smooth_dt must be F64 or F32");
   PUM_CHECK(sp->g_dt == PUM_F64 || sp->g_dt == PUM_F32 || sp->g_dt == PUM_BF16, PUM_ERR_INVALID_ARG, "g_dt");
@@ -221,7 +230,7 @@ const Bsr* select_matrix(const pum_hier* h, int level, int which) {
 
 // ---- persistence helpers
 const uint32_t kMagic = 0x484D5550u;  // "PUMH"
-const uint32_t kVersion = 2;
+const uint32_t kVersion = 3;
 
 void wr(FILE* f, const void* p, size_t n) {
   PUM_CHECK(n == 0 || fwrite(p, 1, n, f) == n, PUM_ERR_IO, "write failed");
@@ -485,6 +494,31 @@ pum_status pcg_solve(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_
   });
 }
 
+pum_status bicgstab_solve(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_report* rep) {
+  if (!ctx) return PUM_ERR_INVALID_ARG;
+  return guard(ctx, [&]() {
+    check_ready(h);
+    check_vec(b, "b");
+    check_vec(x, "x");
+    PUM_CHECK(rep && rep->maxit >= 0 && rep->rtol >= 0.0, PUM_ERR_INVALID_ARG, "pcg_report");
+    const pum_status st = bicgstab_impl(ctx, h, b, x, rep);
+    PUM_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (st == PUM_ERR_NOCONV) ctx->last_error = "BiCGStab reached maxit before rtol";
+    return st;
+  });
+}
+
+pum_status pum_convergence_factor(pum_ctx* ctx, pum_hier* h, const double* e0, int n_cycles, double* rho) {
+  if (!ctx) return PUM_ERR_INVALID_ARG;
+  return guard(ctx, [&]() {
+    check_ready(h);
+    check_vec(e0, "e0");
+    PUM_CHECK(rho != nullptr && n_cycles >= 1, PUM_ERR_INVALID_ARG, "n_cycles >= 1 and a rho pointer");
+    *rho = convergence_factor_impl(ctx, h, e0, n_cycles);
+    return PUM_OK;
+  });
+}
+
 pum_status pum_residual(pum_ctx* ctx, pum_hier* h, int level, const double* b, const double* x, double* r) {
   if (!ctx) return PUM_ERR_INVALID_ARG;
   return guard(ctx, [&]() {
@@ -731,6 +765,8 @@ pum_status pum_hier_destroy(pum_hier* h) {
   graph_destroy(h->vgraph);
   for (auto& L : h->lv) free_level(L);
   for (auto& w : h->w64)
+    if (w) cudaFree(w);
+  for (auto& w : h->wb)
     if (w) cudaFree(w);
   if (h->coarse.L) cudaFree(h->coarse.L);
   delete h;

@@ -189,6 +189,8 @@ struct pum_hier {
   std::vector<double> mu;  // Chebyshev mu_i, i = 1..k
   // FP64 work vectors of the finest level (PCG, conversions)
   double* w64[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // more of them for BiCGStab and the convergence factor, allocated on first use
+  double* wb[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   pum::GraphCache vgraph;  // captured V-cycle
   bool sell = true;        // sliced layouts for the large levels' FP32 products
 };
@@ -262,7 +264,7 @@ void coarse_factor(pum_ctx* ctx, pum_hier* h);
 // Smoother / cycle (solve.cu)
 void apply_M(pum_ctx* ctx, pum_hier* h, int l, const void* r, void* z, int tk_first);
 void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_zero, void* x_acc, int acc_dt,
-           bool acc_set, void* x_acc_split = nullptr);
+           bool acc_set, void* x_acc_split = nullptr, int steps = 0);
 void vcycle_level(pum_ctx* ctx, pum_hier* h, int l);
 void coarse_solve(pum_ctx* ctx, pum_hier* h, const void* b, void* x, int vdt);
 

@@ -72,13 +72,16 @@ void apply_M(pum_ctx* ctx, pum_hier* h, int l, const void* r, void* z, int) {
   fsai_apply_epi(ctx, h, l, r, EPI_SET, e);
 }
 
-// Algorithm 3 on level l for A x = rhs with iterate x (in place); x_zero: x0 = 0.  When
-// x_acc is given, every update of x is also added to x_acc (the correction form below).
+// Algorithm 3 on level l for A x = rhs with iterate x (in place), `steps` steps (0: degree_k);
+// x_zero: x0 = 0.  When x_acc is given, every update of x is also added to x_acc (the correction
+// form below).  Richardson smoothing (Section 3.1) is the same loop with p = M r and x = x + p:
+// mu^2 = 0 and d mu = 1 in the fused update.
 void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_zero, void* x_acc, int acc_dt,
-           bool acc_set, void* x_acc_split) {
+           bool acc_set, void* x_acc_split, int steps) {
   Level& L = h->lv[l];
   const int vdt = L.vdt;
-  const int k = h->sp.degree_k;
+  const int k = steps > 0 ? steps : h->sp.degree_k;
+  const bool richardson = h->sp.smoother == PUM_SMOOTHER_RICHARDSON;
   const double dd = 4.0 / L.beta;  // d = 4 / beta
   const bool fin = (l == 0);
   for (int i = 1; i <= k; ++i) {
@@ -97,13 +100,13 @@ void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_ze
     e.x2s = x_acc_split;
     e.x2dt = acc_dt;
     e.x2_set = acc_set && x_zero && i == 1;
-    e.dmu = dd * h->mu[i - 1];
+    e.dmu = richardson ? 1.0 : dd * h->mu[i - 1];
     int epi;
     if (i == 1) {
       epi = x_zero ? EPI_CHEB_FIRST0 : EPI_CHEB_FIRST;  // p = M r; x = x0 + d mu p
     } else {
       epi = EPI_CHEB;  // p = mu^2 p + M r; mu <- 1/(2 - mu); x = x + d mu p
-      e.mu2 = h->mu[i - 2] * h->mu[i - 2];
+      e.mu2 = richardson ? 0.0 : h->mu[i - 2] * h->mu[i - 2];
     }
     fsai_apply_epi(ctx, h, l, src, epi, e);
   }
@@ -168,7 +171,9 @@ void vcycle_level(pum_ctx* ctx, pum_hier* h, int l) {
   const bool corr = vdt == PUM_F32 && h->sp.mixed_levels > 0;
   const Bsr& Ar = corr ? L.A : smoothA(h, l);  // operator of the two accurate residuals
   const int tk_r = l == 0 ? (corr ? PUM_TK_RESID64 : PUM_TK_RESID) : -1;
-  cheb4(ctx, h, l, L.b, L.x, true, nullptr, -1, false);  // pre-smoothing from x0 = 0
+  const bool v2k0 = h->sp.cycle == PUM_CYCLE_V2K0;
+  // pre-smoothing from x0 = 0: k steps, or 2k for V(2k,0)
+  cheb4(ctx, h, l, L.b, L.x, true, nullptr, -1, false, nullptr, v2k0 ? 2 * h->sp.degree_k : 0);
   EpiArgs e{};
   e.y = L.r;
   e.b = L.b;
@@ -180,6 +185,7 @@ void vcycle_level(pum_ctx* ctx, pum_hier* h, int l) {
   EpiArgs pa{};
   pa.y = L.x;
   bsr_mv(ctx, P, vdt, C.x, EPI_ADD, pa);  // x += P x_c
+  if (v2k0) return;  // V(2k,0): no post-smoothing
   if (!corr) {
     cheb4(ctx, h, l, L.b, L.x, false, nullptr, -1, false);  // post-smoothing, same polynomial
     return;
@@ -287,8 +293,10 @@ static void vcycle_mixed(pum_ctx* ctx, pum_hier* h, int l, const double* r, doub
   }
   Level& C = h->lv[l + 1];
   const int tk = l == 0 ? PUM_TK_RESID64 : -1;
-  convert_vec(ctx, L.b, PUM_F32, r, PUM_F64, N);             // FP32 right-hand side of the smoother
-  cheb4(ctx, h, l, L.b, L.e, true, z, PUM_F64, true, L.zs);  // pre-smoothing: z = e in FP64
+  const bool v2k0 = h->sp.cycle == PUM_CYCLE_V2K0;
+  convert_vec(ctx, L.b, PUM_F32, r, PUM_F64, N);  // FP32 right-hand side of the smoother
+  // pre-smoothing: z = e in FP64 (k steps, 2k for V(2k,0))
+  cheb4(ctx, h, l, L.b, L.e, true, z, PUM_F64, true, L.zs, v2k0 ? 2 * h->sp.degree_k : 0);
   EpiArgs er{};
   er.y = L.r;
   er.b = r;
@@ -324,6 +332,7 @@ static void vcycle_mixed(pum_ctx* ctx, pum_hier* h, int l, const double* r, doub
     pa.ydt = PUM_F64;
     bsr_mv(ctx, L.Ps, PUM_F32, C.x, EPI_ADD, pa);  // z += P x_c
   }
+  if (v2k0) return;  // V(2k,0): no post-smoothing
   EpiArgs cr{};
   cr.y = L.c;
   cr.b = r;
@@ -470,6 +479,230 @@ pum_status pcg_impl(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_r
   graph_harvest(ctx, h);
   check_device_status(ctx);
   return PUM_ERR_NOCONV;
+}
+
+
+// ----------------------------------------------------------------------------- BiCGStab
+
+// Device scalar slots of BiCGStab and of the convergence factor (after the PCG ones).
+enum { B_RHO = 6, B_RHO_OLD = 7, B_ALPHA = 8, B_OMEGA = 9, B_RV = 10, B_TS = 11, B_TT = 12, B_SS = 13, B_RR = 14,
+       B_E0 = 15, B_EN = 16 };
+
+__global__ void k_bicg_init(double* scal) {
+  scal[B_RHO_OLD] = 1.0;
+  scal[B_ALPHA] = 1.0;
+  scal[B_OMEGA] = 1.0;
+}
+
+// p = r + beta (p - omega v), beta = (rho / rho_old) (alpha / omega)
+__global__ void k_bicg_p(double* __restrict__ p, const double* __restrict__ r, const double* __restrict__ v,
+                         const double* __restrict__ scal, int64_t n) {
+  const double beta = (scal[B_RHO] / scal[B_RHO_OLD]) * (scal[B_ALPHA] / scal[B_OMEGA]);
+  const double omega = scal[B_OMEGA];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i] - omega * v[i], r[i]);
+}
+
+template <int NT>
+__device__ __forceinline__ void block_partial(double sum, double* partials) {
+  __shared__ double red[NT / 32];
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < NT / 32; ++w) t += red[w];
+    partials[blockIdx.x] = t;
+  }
+}
+
+// alpha = rho / (r^ . v); s = r - alpha v; partial sums of s . s
+__global__ void k_bicg_s(double* __restrict__ s, const double* __restrict__ r, const double* __restrict__ v,
+                         double* __restrict__ scal, int64_t n, double* __restrict__ partials) {
+  const double alpha = scal[B_RHO] / scal[B_RV];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double si = fma(-alpha, v[i], r[i]);
+    s[i] = si;
+    acc = fma(si, si, acc);
+  }
+  block_partial<256>(acc, partials);
+  if (blockIdx.x == 0 && threadIdx.x == 0) scal[B_ALPHA] = alpha;
+}
+
+// omega = (t . s) / (t . t); x += alpha ph + omega sh; r = s - omega t; partial sums of r . r
+__global__ void k_bicg_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ ph,
+                          const double* __restrict__ sh, const double* __restrict__ s, const double* __restrict__ t,
+                          double* __restrict__ scal, int64_t n, double* __restrict__ partials) {
+  const double alpha = scal[B_ALPHA];
+  const double omega = scal[B_TS] / scal[B_TT];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(omega, sh[i], fma(alpha, ph[i], x[i]));
+    const double ri = fma(-omega, t[i], s[i]);
+    r[i] = ri;
+    acc = fma(ri, ri, acc);
+  }
+  block_partial<256>(acc, partials);
+  if (blockIdx.x == 0 && threadIdx.x == 0) scal[B_OMEGA] = omega;
+}
+
+// x += scal[slot] y (slot < 0: factor 1)
+__global__ void k_axpy_slot(double* __restrict__ x, const double* __restrict__ y, const double* __restrict__ scal,
+                            int slot, int64_t n) {
+  const double a = slot >= 0 ? scal[slot] : 1.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = fma(a, y[i], x[i]);
+}
+
+static void ensure_wb(pum_hier* h, int64_t N) {
+  for (auto& w : h->wb)
+    if (!w && cudaMalloc(&w, sizeof(double) * N) != cudaSuccess) {
+      cudaGetLastError();
+      w = nullptr;
+      throw Error{PUM_ERR_OOM, "Krylov work vectors: device allocation failed"};
+    }
+}
+
+// z = B r through the fixed pair (vin, vout), so that the captured V-cycle graph is reused.
+static void cycle_via(pum_ctx* ctx, pum_hier* h, const double* r, double* z, int64_t N) {
+  double *vin = h->w64[0], *vout = h->w64[1];
+  PUM_CUDA(cudaMemcpyAsync(vin, r, sizeof(double) * N, cudaMemcpyDeviceToDevice, ctx->stream));
+  vcycle64(ctx, h, vin, vout);
+  PUM_CUDA(cudaMemcpyAsync(z, vout, sizeof(double) * N, cudaMemcpyDeviceToDevice, ctx->stream));
+}
+
+pum_status bicgstab_impl(pum_ctx* ctx, pum_hier* h, const double* b, double* x, pcg_report* rep) {
+  Level& L0 = h->lv[0];
+  const int64_t N = (int64_t)L0.n * L0.d;
+  cudaStream_t st = ctx->stream;
+  ensure_wb(h, N);
+  double *r = h->wb[0], *rhat = h->wb[1], *p = h->wb[2], *v = h->wb[3], *s = h->wb[4], *t = h->wb[5],
+         *ph = h->wb[6], *sh = h->wb[7];
+  const int grid = (int)std::min<int64_t>((N + 255) / 256, 1024);
+  PUM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * N, st));
+  PUM_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  PUM_CUDA(cudaMemcpyAsync(rhat, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  PUM_CUDA(cudaMemsetAsync(p, 0, sizeof(double) * N, st));
+  PUM_CUDA(cudaMemsetAsync(v, 0, sizeof(double) * N, st));
+  dot(ctx, b, b, N, S_BB);
+  k_bicg_init<<<1, 1, 0, st>>>(ctx->scal);
+  count_launch(ctx);
+  PUM_CUDA(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * kScalSlots, cudaMemcpyDeviceToHost, st));
+  PUM_CUDA(cudaStreamSynchronize(st));
+  const double nb = std::sqrt(ctx->h_scal[S_BB]);
+  rep->iters = 0;
+  rep->converged = 0;
+  rep->final_relres = 1.0;
+  if (rep->hist && rep->maxit >= 0) rep->hist[0] = 1.0;
+  if (nb == 0.0) {
+    rep->converged = 1;
+    rep->final_relres = 0.0;
+    return PUM_OK;
+  }
+  auto breakdown = [&](int it, const char* what) {
+    rep->iters = it;
+    check_device_status(ctx);
+    return Error{PUM_ERR_BREAKDOWN, std::string("BiCGStab breakdown: ") + what};
+  };
+  for (int it = 1; it <= rep->maxit; ++it) {
+    dot(ctx, rhat, r, N, B_RHO);
+    k_bicg_p<<<grid, 256, 0, st>>>(p, r, v, ctx->scal, N);
+    count_launch(ctx);
+    cycle_via(ctx, h, p, ph, N);  // p^ = B p
+    EpiArgs e{};
+    e.y = v;
+    bsr_mv(ctx, L0.A, PUM_F64, ph, EPI_SET, e);  // v = A p^
+    dot(ctx, rhat, v, N, B_RV);
+    k_bicg_s<<<grid, 256, 0, st>>>(s, r, v, ctx->scal, N, ctx->partials);
+    count_launch(ctx);
+    reduce_partials(ctx, grid, B_SS);
+    PUM_CUDA(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * kScalSlots, cudaMemcpyDeviceToHost, st));
+    PUM_CUDA(cudaStreamSynchronize(st));
+    const double rho = ctx->h_scal[B_RHO], rv = ctx->h_scal[B_RV];
+    if (!(rho != 0.0 && rv != 0.0 && std::isfinite(rho) && std::isfinite(rv))) throw breakdown(it, "r^.r or r^.v");
+    const double srel = std::sqrt(ctx->h_scal[B_SS]) / nb;
+    if (srel <= rep->rtol) {  // the half step already converged: x += alpha p^
+      k_axpy_slot<<<grid, 256, 0, st>>>(x, ph, ctx->scal, B_ALPHA, N);
+      count_launch(ctx);
+      if (rep->hist) rep->hist[it] = srel;
+      rep->iters = it;
+      rep->final_relres = srel;
+      rep->converged = 1;
+      graph_harvest(ctx, h);
+      check_device_status(ctx);
+      return PUM_OK;
+    }
+    cycle_via(ctx, h, s, sh, N);  // s^ = B s
+    e.y = t;
+    bsr_mv(ctx, L0.A, PUM_F64, sh, EPI_SET, e);  // t = A s^
+    dot(ctx, t, s, N, B_TS);
+    dot(ctx, t, t, N, B_TT);
+    k_bicg_xr<<<grid, 256, 0, st>>>(x, r, ph, sh, s, t, ctx->scal, N, ctx->partials);
+    count_launch(ctx);
+    reduce_partials(ctx, grid, B_RR);
+    k_scal_move<<<1, 1, 0, st>>>(ctx->scal, B_RHO_OLD, B_RHO);
+    count_launch(ctx);
+    PUM_CUDA(cudaGetLastError());
+    PUM_CUDA(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * kScalSlots, cudaMemcpyDeviceToHost, st));
+    PUM_CUDA(cudaStreamSynchronize(st));
+    const double tt = ctx->h_scal[B_TT], rr = ctx->h_scal[B_RR];
+    if (!(tt > 0.0 && std::isfinite(rr))) throw breakdown(it, "t.t");
+    const double rel = std::sqrt(rr) / nb;
+    if (rep->hist) rep->hist[it] = rel;
+    rep->iters = it;
+    rep->final_relres = rel;
+    if (rel <= rep->rtol) {
+      rep->converged = 1;
+      graph_harvest(ctx, h);
+      check_device_status(ctx);
+      return PUM_OK;
+    }
+  }
+  graph_harvest(ctx, h);
+  check_device_status(ctx);
+  return PUM_ERR_NOCONV;
+}
+
+// rho_A of the stationary cycle: e_j = e_{j-1} + B (-A e_{j-1}), the energy ratio over n cycles.
+double convergence_factor_impl(pum_ctx* ctx, pum_hier* h, const double* e0, int n_cycles) {
+  Level& L0 = h->lv[0];
+  const int64_t N = (int64_t)L0.n * L0.d;
+  cudaStream_t st = ctx->stream;
+  ensure_wb(h, N);
+  double *e = h->wb[0], *q = h->wb[1], *zero = h->wb[2], *ar = h->wb[3], *z = h->wb[4];
+  const unsigned mvgrid = (unsigned)((N + 255) / 256);
+  PUM_CHECK(mvgrid <= (1u << 16), PUM_ERR_UNSUPPORTED, "convergence factor: problem too large for the partials");
+  const int grid = (int)std::min<int64_t>((N + 255) / 256, 1024);
+  PUM_CUDA(cudaMemcpyAsync(e, e0, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  PUM_CUDA(cudaMemsetAsync(zero, 0, sizeof(double) * N, st));
+  auto energy = [&](int slot) {  // e^T A e
+    EpiArgs d{};
+    d.y = q;
+    d.partials = ctx->partials;
+    bsr_mv(ctx, L0.A, PUM_F64, e, EPI_DOT, d);
+    reduce_partials(ctx, (int)mvgrid, slot);
+  };
+  energy(B_E0);
+  for (int j = 0; j < n_cycles; ++j) {
+    EpiArgs rs{};
+    rs.y = ar;
+    rs.b = zero;
+    bsr_mv(ctx, L0.A, PUM_F64, e, EPI_RESID, rs);  // -A e
+    cycle_via(ctx, h, ar, z, N);
+    k_axpy_slot<<<grid, 256, 0, st>>>(e, z, ctx->scal, -1, N);
+    count_launch(ctx);
+  }
+  energy(B_EN);
+  PUM_CUDA(cudaGetLastError());
+  PUM_CUDA(cudaMemcpyAsync(ctx->h_scal, ctx->scal, sizeof(double) * kScalSlots, cudaMemcpyDeviceToHost, st));
+  PUM_CUDA(cudaStreamSynchronize(st));
+  graph_harvest(ctx, h);
+  check_device_status(ctx);
+  const double e0n = ctx->h_scal[B_E0], enn = ctx->h_scal[B_EN];
+  PUM_CHECK(e0n > 0.0 && enn >= 0.0 && std::isfinite(enn), PUM_ERR_BREAKDOWN,
+            "convergence factor: e^T A e not positive (e0 = 0, or A not SPD)");
+  return std::pow(enn / e0n, 1.0 / (2.0 * n_cycles));
 }
 
 }  // namespace pum

@@ -246,6 +246,56 @@ def test_pcg_histories_match_oracle(lib, static_pair, small_biharmonic):
     assert norm_rel(host(x), res.x) <= 1e-9
 
 
+# --------------------------------------------- cycle and smoother variants (Section 5, NEXT-3)
+
+VARIANTS = [("cheb4", "v2k0"), ("richardson", "vkk"), ("richardson", "v2k0")]
+
+
+@pytest.fixture(scope="module")
+def variant_pairs(lib, ctx, small_biharmonic):
+    out = {}
+    for smoother, cycle in VARIANTS + [("cheb4", "vkk")]:
+        H = hier_from_oracle(lib, ctx, small_biharmonic)
+        H.setup(p0="lower", adaptive=False, k=PR.cheb_k, smoother=smoother, cycle=cycle)
+        ref = solver.build_setup(small_biharmonic, k=PR.cheb_k, mode="static", P0="lower")
+        ref.smoother, ref.cycle = smoother, cycle
+        out[(smoother, cycle)] = (H, ref)
+    return out
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_variant_cycles_match_oracle(variant_pairs, variant):
+    """Richardson smoothing and the V(2k,0) cycle: one cycle on the GPU equals the oracle's."""
+    H, ref = variant_pairs[variant]
+    r = pin.normal_vector(PR.n_dofs, 71)
+    z = cuda(np.zeros_like(r))
+    H.vcycle(cuda(r), z)
+    assert norm_rel(host(z), solver.vcycle(ref, r)) <= TOL_VECTOR
+
+
+@pytest.mark.parametrize("variant", VARIANTS + [("cheb4", "vkk")])
+def test_convergence_factor_matches_oracle(variant_pairs, small_biharmonic, variant):
+    """rho_A of the stationary cycle (the paper's figures' measure), GPU against oracle."""
+    H, ref = variant_pairs[variant]
+    e0 = pin.uniform_vector(PR.n_dofs, 5)
+    rho = H.convergence_factor(cuda(e0), 8)
+    rho_ref = solver.convergence_factor(ref, e0, 8)
+    assert abs(rho - rho_ref) <= 1e-10 * rho_ref
+
+
+def test_bicgstab_with_v2k0_matches_oracle(variant_pairs, small_biharmonic):
+    """BiCGStab preconditioned by the non-symmetric V(2k,0) cycle: same iterations, histories
+    within 1e-10, solution of the oracle's run."""
+    H, ref = variant_pairs[("cheb4", "v2k0")]
+    h = small_biharmonic
+    x = cuda(np.zeros_like(h.b))
+    rep = H.bicgstab(cuda(h.b), x, rtol=1e-8, maxit=100)
+    res = solver.solve_bicgstab(ref, h.b, rtol=1e-8)
+    assert rep["converged"] and rep["iters"] == res.iters
+    assert np.max(np.abs(np.array(rep["history"]) - np.array(res.history))) <= 1e-10
+    assert norm_rel(host(x), res.x) <= 1e-8
+
+
 def test_end_to_end_gpu_assembly_and_setup(lib, ctx, small_biharmonic):
     """GPU assembly + GPU static FSAI + PCG against the oracle's whole pipeline."""
     import torch
