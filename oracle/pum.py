@@ -171,25 +171,59 @@ def max_order(op) -> int:
     return max(max(al, be) for (al, be) in op)
 
 
+ISOTROPIC = (1.0, 0.0, 1.0)
+
+
+def anisotropy(kappa: float, theta: float) -> tuple:
+    """(S11, S12, S22) of S = R(theta) diag(kappa, 1) R(theta)^T (Example 5.2)."""
+    c, s = np.cos(theta), np.sin(theta)
+    return (kappa * c * c + s * s, (kappa - 1.0) * c * s, kappa * s * s + c * c)
+
+
+def op_aniso_lap(S):
+    """tr(S H(w)) = S11 w_xx + 2 S12 w_xy + S22 w_yy, the Laplacian of Example 5.2."""
+    ops = {(2, 0): S[0], (1, 1): 2.0 * S[1], (0, 2): S[2]}
+    return {k: c for k, c in ops.items() if c != 0.0}
+
+
 @dataclasses.dataclass(frozen=True)
 class Equation:
-    """order = 4: Delta^2 u = f (Example 5.1); order = 6: -Delta^3 u = f (Example 5.4)."""
+    """order = 4: Delta^2 u = f (Example 5.1), or with S != I the anisotropic S_ij S_kl u_,ijkl = f
+    of Example 5.2 (Delta w replaced by tr(S H(w)), grad w . n by grad w . (S n)); order = 6:
+    -Delta^3 u = f (Example 5.4)."""
     order: int
+    S: tuple = ISOTROPIC
+
+    def __post_init__(self):
+        if self.order != 4 and tuple(self.S) != ISOTROPIC:
+            raise ValueError("anisotropy is defined for the biharmonic equation only (Example 5.2)")
+
+    def lap(self):
+        return OP_LAP if tuple(self.S) == ISOTROPIC else op_aniso_lap(self.S)
+
+    def conormal(self, n):
+        """S n (n itself when isotropic)."""
+        if tuple(self.S) == ISOTROPIC:
+            return n
+        return (self.S[0] * n[0] + self.S[1] * n[1], self.S[1] * n[0] + self.S[2] * n[1])
 
     def interior_pairs(self):
         """Pairs (op on v, op on u, coefficient) of the domain integral of a_n(v, u)."""
         if self.order == 4:
-            return [(OP_LAP, OP_LAP, 1.0)]
+            L = self.lap()
+            return [(L, L, 1.0)]
         gl = (op_dx(OP_LAP), op_dy(OP_LAP))
         return [(gl[0], gl[0], 1.0), (gl[1], gl[1], 1.0)]
 
     def boundary_pairs(self, n, gamma):
         """Pairs (op on v, op on u, coefficient) of the boundary integrals of a_n(v, u)."""
-        dn = op_dn(OP_I, n)
         if self.order == 4:
-            dnlap = op_dn(OP_LAP, n)
+            L, sn = self.lap(), self.conormal(n)
+            dn = op_dn(OP_I, sn)
+            dnlap = op_dn(L, sn)
             return [(OP_I, OP_I, gamma[0]), (OP_I, dnlap, 1.0), (dnlap, OP_I, 1.0),
-                    (dn, dn, gamma[1]), (dn, OP_LAP, -1.0), (OP_LAP, dn, -1.0)]
+                    (dn, dn, gamma[1]), (dn, L, -1.0), (L, dn, -1.0)]
+        dn = op_dn(OP_I, n)
         dnlap = op_dn(OP_LAP, n)
         dnbil = op_dn(OP_BILAP, n)
         return [(OP_I, OP_I, gamma[0]), (OP_I, dnbil, -1.0), (dnbil, OP_I, -1.0),
@@ -198,10 +232,11 @@ class Equation:
 
     def load_boundary_terms(self, n, gamma):
         """(index of boundary datum g_j, op on v, coefficient) of l_n(v)."""
-        dn = op_dn(OP_I, n)
         if self.order == 4:
-            return [(0, OP_I, gamma[0]), (0, op_dn(OP_LAP, n), 1.0),
-                    (1, dn, gamma[1]), (1, OP_LAP, -1.0)]
+            L, sn = self.lap(), self.conormal(n)
+            return [(0, OP_I, gamma[0]), (0, op_dn(L, sn), 1.0),
+                    (1, op_dn(OP_I, sn), gamma[1]), (1, L, -1.0)]
+        dn = op_dn(OP_I, n)
         return [(0, OP_I, gamma[0]), (0, op_dn(OP_BILAP, n), -1.0),
                 (1, dn, gamma[1]), (1, OP_BILAP, 1.0),
                 (2, OP_LAP, gamma[2]), (2, op_dn(OP_LAP, n), -1.0)]
@@ -213,11 +248,18 @@ class Equation:
 NITSCHE_CONSTANTS = {4: (4.0, 2.0), 6: (1.0e4, 1.0e2, 1.0)}
 
 
-def nitsche_gamma(order: int, p: int, m: int, constants=None) -> list[float]:
-    """Penalties gamma^(j) = C_j (p+1)^2 h^-(order-1-2j), j < order/2 (Examples 5.1, 5.4)."""
+def nitsche_gamma(order: int, p: int, m: int, constants=None, S=ISOTROPIC) -> list[float]:
+    """Penalties gamma^(j) = C_j (p+1)^2 h^-(order-1-2j), j < order/2 (Examples 5.1, 5.4).
+
+    Anisotropic biharmonic (Example 5.2): the consistency terms int v grad(tr(S H u)) . (S n)
+    carry |S|^2 against the penalty int gamma^(0) u v, so gamma^(0) is scaled by |S|_2^2 (the
+    penalty on grad u . (S n) already carries S)."""
     h = 1.0 / m
     C = NITSCHE_CONSTANTS[order] if constants is None else constants
-    return [C[j] * (p + 1) ** 2 * h ** (-(order - 1 - 2 * j)) for j in range(order // 2)]
+    g = [C[j] * (p + 1) ** 2 * h ** (-(order - 1 - 2 * j)) for j in range(order // 2)]
+    if tuple(S) != ISOTROPIC:
+        g[0] *= float(np.max(np.linalg.eigvalsh(np.array([[S[0], S[1]], [S[1], S[2]]])))) ** 2
+    return g
 
 
 # ---------------------------------------------------------------------------
@@ -277,7 +319,7 @@ class Assembled:
 
 
 def assemble(m: int, p: int, order: int, gamma, f=None, g=None, q: int | None = None,
-             with_mass: bool = True, rows=None) -> Assembled:
+             with_mass: bool = True, rows=None, S=ISOTROPIC) -> Assembled:
     """Stiffness A, load b and mass matrix M of the PUM space of level m.
 
     f(x, y) is the source, g = [g0, g1, (g2)] the boundary data (callables of
@@ -287,7 +329,7 @@ def assemble(m: int, p: int, order: int, gamma, f=None, g=None, q: int | None = 
     (the other rows of A, M and b stay empty / zero).
     """
     keep = None if rows is None else set(int(r) for r in rows)
-    eq = Equation(order)
+    eq = Equation(order, tuple(S))
     d = local_dim(p)
     exps = basis_exponents(p)
     q = q or p + 6
@@ -519,10 +561,10 @@ class Hierarchy:
 
 
 def build_hierarchy(m: int, p: int, order: int, n_levels: int, f=None, with_mass: bool = False,
-                    constants=None) -> Hierarchy:
+                    constants=None, S=ISOTROPIC) -> Hierarchy:
     """Finest-level assembly plus Galerkin coarse operators A_{l-1} = P^T A_l P (Section 5)."""
-    gamma = nitsche_gamma(order, p, m, constants)
-    asm = assemble(m, p, order, gamma, f=f, with_mass=with_mass)
+    gamma = nitsche_gamma(order, p, m, constants, S)
+    asm = assemble(m, p, order, gamma, f=f, with_mass=with_mass, S=S)
     ms, As, Ps = [m], [asm.A], []
     for _ in range(n_levels - 1):
         P = prolongation(ms[-1], p)

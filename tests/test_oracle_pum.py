@@ -201,6 +201,68 @@ def test_patch_test_fails_with_a_flipped_boundary_sign():
     assert np.max(np.abs(wrong - exact)) > 1e-4
 
 
+# ------------------------------------------------- anisotropic biharmonic (Example 5.2)
+
+S_ANISO = pum.anisotropy(10.0, np.pi / 3)
+
+
+def test_anisotropy_tensor():
+    """S = R(theta) diag(kappa, 1) R(theta)^T: eigenvalue kappa along (cos theta, sin theta)."""
+    S = np.array([[S_ANISO[0], S_ANISO[1]], [S_ANISO[1], S_ANISO[2]]])
+    v = np.array([np.cos(np.pi / 3), np.sin(np.pi / 3)])
+    assert np.allclose(S @ v, 10.0 * v, atol=1e-14)
+    assert np.allclose(np.linalg.eigvalsh(S), [1.0, 10.0], atol=1e-13)
+    assert pum.anisotropy(1.0, 0.7) == pytest.approx(pum.ISOTROPIC, abs=1e-15)
+
+
+def test_isotropic_tensor_gives_the_isotropic_form_bitwise():
+    m, p = 4, 3
+    g = pum.nitsche_gamma(4, p, m)
+    f = pum.fourier_source(np.ones((2, 2)), 2.0)
+    a = pum.assemble(m, p, 4, g, f=f, with_mass=False)
+    b = pum.assemble(m, p, 4, pum.nitsche_gamma(4, p, m, S=pum.ISOTROPIC), f=f, with_mass=False, S=pum.ISOTROPIC)
+    assert np.array_equal(a.A.blocks, b.A.blocks) and np.array_equal(a.b, b.b)
+
+
+@pytest.mark.parametrize("m", [2, 4, 8])
+def test_anisotropic_stiffness_spd(m):
+    """With gamma^(0) scaled by |S|^2 the anisotropic Nitsche matrix is SPD (kappa = 10)."""
+    A = pum.assemble(m, 3, 4, pum.nitsche_gamma(4, 3, m, S=S_ANISO), with_mass=False, S=S_ANISO).A.to_dense()
+    assert np.max(np.abs(A - A.T)) <= 1e-14 * np.max(np.abs(A))
+    np.linalg.cholesky(A)
+
+
+@pytest.mark.parametrize("m", [2, 4])
+def test_anisotropic_patch_test(m):
+    """Example 5.2: a cubic u solves S_ij S_kl u_,ijkl = f with f from u's fourth derivatives
+    (zero for cubics, so take p = 4 and a quartic), g_0 = u, g_1 = grad u . (S n): the Nitsche
+    solution reproduces u exactly.  A wrong S in any consistency term breaks this."""
+    p = 4
+    C = _rand_poly(p, 31 + m)
+    s11, s12, s22 = S_ANISO
+    # S_ij S_kl d_ijkl u = (s11 d_xx + 2 s12 d_xy + s22 d_yy)^2 u
+    coef = {(4, 0): s11 * s11, (3, 1): 4 * s11 * s12, (2, 2): 2 * s11 * s22 + 4 * s12 * s12,
+            (1, 3): 4 * s12 * s22, (0, 4): s22 * s22}
+    f = lambda x, y: sum(c * _ev(C, x, y, a, b) for (a, b), c in coef.items())
+
+    def sn(x, y):
+        nx = np.where(x <= 0.0, -1.0, np.where(x >= 1.0, 1.0, 0.0))
+        ny = np.where(y <= 0.0, -1.0, np.where(y >= 1.0, 1.0, 0.0))
+        return s11 * nx + s12 * ny, s12 * nx + s22 * ny
+
+    def g1(x, y):
+        a, b = sn(x, y)
+        return a * _ev(C, x, y, 1, 0) + b * _ev(C, x, y, 0, 1)
+    g = [lambda x, y: _ev(C, x, y), g1]
+    asm = pum.assemble(m, p, 4, pum.nitsche_gamma(4, p, m, S=S_ANISO), f=f, g=g, with_mass=False, S=S_ANISO)
+    A = asm.A.to_dense()
+    u = np.linalg.solve(A, asm.b)
+    exact = pum.local_projection(m, p, lambda x, y: _ev(C, x, y))
+    assert np.max(np.abs(u - exact)) <= 100 * np.linalg.cond(A) * 2.2e-16 * np.max(np.abs(exact))
+    iso = pum.assemble(m, p, 4, pum.nitsche_gamma(4, p, m, S=S_ANISO), f=f, g=g, with_mass=False)
+    assert np.max(np.abs(np.linalg.solve(iso.A.to_dense(), iso.b) - exact)) > 1e-3 * np.max(np.abs(exact))
+
+
 # --------------------------------------------------------------------------- P-6
 
 @pytest.mark.parametrize("order,p", [(4, 3), (6, 5)])
