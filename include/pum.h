@@ -83,6 +83,9 @@ typedef struct {
   const double *f_coef; /* host, f_modes*f_modes coefficients c_ab (row a-1, column b-1) */
   int32_t f_modes;      /* f = sum c_ab (a^2+b^2)^(-f_decay/2) sin(a pi x) sin(b pi y)   */
   double f_decay;
+  double aniso[3];      /* S11, S12, S22 of the SPD tensor S of Example 5.2 (equation 4 only):
+                           S_ij S_kl u_,ijkl = f, Delta -> tr(S H), grad . n -> grad . (S n),
+                           gamma^(0) scaled by |S|_2^2; all zero: isotropic (S = I)          */
 } pum_problem;
 
 enum { PUM_P0_LOWER = 0, PUM_P0_DIAG = 1 };

@@ -123,12 +123,15 @@ class Hierarchy:
     # ---- construction
     @classmethod
     def assemble(cls, ctx: Context, equation: int, p: int, finest_m: int, n_levels: int, f_coef=None,
-                 f_decay: float = 2.0, nitsche=(0.0, 0.0, 0.0), quad_pts: int = 0, b=None):
+                 f_decay: float = 2.0, nitsche=(0.0, 0.0, 0.0), quad_pts: int = 0, b=None, aniso=None):
+        """aniso: (S11, S12, S22) of the anisotropy tensor of Example 5.2 (biharmonic only)."""
         pr = _lib.Problem()
         pr.equation, pr.p, pr.finest_m, pr.n_levels = equation, p, finest_m, n_levels
         for j in range(3):
             pr.nitsche_c[j] = float(nitsche[j]) if j < len(nitsche) else 0.0
         pr.quad_pts = quad_pts
+        for j in range(3):
+            pr.aniso[j] = float(aniso[j]) if aniso is not None else 0.0
         keep = None
         if f_coef is not None:
             keep = np.ascontiguousarray(f_coef, dtype=np.float64)

@@ -32,7 +32,7 @@ class BsrHost(C.Structure):
 class Problem(C.Structure):
     _fields_ = [("equation", c_int32), ("p", c_int32), ("finest_m", c_int32), ("n_levels", c_int32),
                 ("nitsche_c", c_double * 3), ("quad_pts", c_int32), ("f_coef", c_void_p), ("f_modes", c_int32),
-                ("f_decay", c_double)]
+                ("f_decay", c_double), ("aniso", c_double * 3)]
 
 
 class FsaiParams(C.Structure):

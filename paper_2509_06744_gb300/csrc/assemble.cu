@@ -164,6 +164,19 @@ using Op = std::vector<Mono>;
 
 Op op_I() { return {{0, 0, 1.0}}; }
 Op op_lap() { return {{2, 0, 1.0}, {0, 2, 1.0}}; }
+// tr(S H(w)) = S11 w_xx + 2 S12 w_xy + S22 w_yy (Example 5.2); the Laplacian when S = I.
+struct Aniso {
+  bool on = false;
+  double s11 = 1.0, s12 = 0.0, s22 = 1.0;
+};
+Op op_lapS(const Aniso& S) {
+  if (!S.on) return op_lap();
+  Op r;
+  if (S.s11 != 0.0) r.push_back({2, 0, S.s11});
+  if (S.s12 != 0.0) r.push_back({1, 1, 2.0 * S.s12});
+  if (S.s22 != 0.0) r.push_back({0, 2, S.s22});
+  return r;
+}
 Op op_bilap() { return {{4, 0, 1.0}, {2, 2, 2.0}, {0, 4, 1.0}}; }
 Op op_dx(const Op& o) { Op r; for (auto m : o) r.push_back({m.ax + 1, m.ay, m.c}); return r; }
 Op op_dy(const Op& o) { Op r; for (auto m : o) r.push_back({m.ax, m.ay + 1, m.c}); return r; }
@@ -176,17 +189,20 @@ Op op_dn(const Op& o, double nx, double ny) {
 
 struct Pair { Op v, u; double c; };
 
-// a_n(v, u) of Example 5.1 (order 4) and Example 5.4 (order 6): domain part.
-std::vector<Pair> interior_pairs(int order) {
-  if (order == 4) return {{op_lap(), op_lap(), 1.0}};
+// a_n(v, u) of Example 5.1 (order 4; Example 5.2 with S) and Example 5.4 (order 6): domain part.
+std::vector<Pair> interior_pairs(int order, const Aniso& S) {
+  if (order == 4) return {{op_lapS(S), op_lapS(S), 1.0}};
   return {{op_dx(op_lap()), op_dx(op_lap()), 1.0}, {op_dy(op_lap()), op_dy(op_lap()), 1.0}};
 }
 
-// Boundary part on an edge with outward normal (nx, ny).
-std::vector<Pair> boundary_pairs(int order, double nx, double ny, const double* g) {
-  const Op I = op_I(), dn = op_dn(op_I(), nx, ny), lap = op_lap(), dnlap = op_dn(op_lap(), nx, ny);
-  if (order == 4)
+// Boundary part on an edge with outward normal (nx, ny); with S the conormal S n replaces n.
+std::vector<Pair> boundary_pairs(int order, double nx, double ny, const double* g, const Aniso& S) {
+  if (order == 4) {
+    const double sx = S.on ? S.s11 * nx + S.s12 * ny : nx, sy = S.on ? S.s12 * nx + S.s22 * ny : ny;
+    const Op I = op_I(), dn = op_dn(op_I(), sx, sy), lap = op_lapS(S), dnlap = op_dn(op_lapS(S), sx, sy);
     return {{I, I, g[0]}, {I, dnlap, 1.0}, {dnlap, I, 1.0}, {dn, dn, g[1]}, {dn, lap, -1.0}, {lap, dn, -1.0}};
+  }
+  const Op I = op_I(), dn = op_dn(op_I(), nx, ny), lap = op_lap(), dnlap = op_dn(op_lap(), nx, ny);
   const Op bil = op_bilap(), dnbil = op_dn(op_bilap(), nx, ny);
   return {{I, I, g[0]},   {I, dnbil, -1.0}, {dnbil, I, -1.0}, {dn, dn, g[1]},      {dn, bil, 1.0},
           {bil, dn, 1.0}, {lap, lap, g[2]}, {lap, dnlap, -1.0}, {dnlap, lap, -1.0}};
@@ -341,6 +357,20 @@ void assemble_finest(pum_ctx* ctx, const pum_problem& pr, Level& L, double* b_de
     const double C = pr.nitsche_c[j] > 0 ? pr.nitsche_c[j] : (order == 4 ? defaults4[j] : defaults6[j]);
     gamma[j] = C * (p + 1) * (p + 1) * std::pow(h, -(order - 1 - 2 * j));
   }
+  Aniso S;
+  S.on = !(pr.aniso[0] == 0.0 && pr.aniso[1] == 0.0 && pr.aniso[2] == 0.0) &&
+         !(pr.aniso[0] == 1.0 && pr.aniso[1] == 0.0 && pr.aniso[2] == 1.0);
+  if (S.on) {
+    S.s11 = pr.aniso[0];
+    S.s12 = pr.aniso[1];
+    S.s22 = pr.aniso[2];
+    PUM_CHECK(order == 4, PUM_ERR_INVALID_ARG, "anisotropy is defined for the biharmonic equation only");
+    PUM_CHECK(S.s11 > 0.0 && S.s22 > 0.0 && S.s11 * S.s22 - S.s12 * S.s12 > 0.0, PUM_ERR_INVALID_ARG,
+              "the anisotropy tensor must be SPD");
+    // the consistency terms carry S twice against the u v penalty: gamma^(0) *= |S|_2^2
+    const double half = 0.5 * (S.s11 + S.s22), rad = std::sqrt(0.25 * (S.s11 - S.s22) * (S.s11 - S.s22) + S.s12 * S.s12);
+    gamma[0] *= (half + rad) * (half + rad);
+  }
   Level1D L1(m);
   Basis1D B(p, NR);
   std::vector<double> gx, gw;
@@ -404,11 +434,11 @@ void assemble_finest(pum_ctx* ctx, const pum_problem& pr, Level& L, double* b_de
   };
   AsmArgs A{};
   A.m = m; A.d = d; A.NP = NP; A.NR = NR;
-  A.n_int = pack(expand(interior_pairs(order)));
+  A.n_int = pack(expand(interior_pairs(order, S)));
   const double normals[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
   for (int e = 0; e < 4; ++e) {
     A.off_edge[e] = (int)terms.size();
-    A.n_edge[e] = pack(expand(boundary_pairs(order, normals[e][0], normals[e][1], gamma)));
+    A.n_edge[e] = pack(expand(boundary_pairs(order, normals[e][0], normals[e][1], gamma, S)));
   }
   for (auto& t : terms) PUM_CHECK(t.v % 8 < NR && t.v / 8 < NR && t.u % 8 < NR && t.u / 8 < NR,
                                   PUM_ERR_INVALID_ARG, "assembly: derivative order beyond table");

@@ -10,6 +10,8 @@ from __future__ import annotations
 
 import dataclasses
 
+import math
+
 import numpy as np
 
 
@@ -103,6 +105,16 @@ BIHARMONIC_256 = Problem("biharmonic p=3 256x256 patches, 9 levels, adaptive blo
                          4, 3, 256, 9, 1, 2.0, "lower", True, 6, 1.0, False, 3, "f64", "f64")
 TRIHARMONIC_256 = Problem("triharmonic p=5 256x256 patches, 9 levels, nested adaptive block-FSAI, Chebyshev-4 k=4",
                           6, 5, 256, 9, 2, 3.0, "diag", True, 6, 1.0, True, 4, "f32", "bf16", 2)
+
+
+def anisotropy_tensor(kappa: float, theta: float) -> tuple:
+    """(S11, S12, S22) of the anisotropic biharmonic workload's tensor S = R diag(kappa, 1) R^T,
+    R the rotation by theta (the problem data of Example 5.2, passed to both implementations)."""
+    c, s = math.cos(theta), math.sin(theta)
+    return (kappa * c * c + s * s, (kappa - 1.0) * c * s, kappa * s * s + c * c)
+
+
+ANISO_KAPPA, ANISO_THETA = 10.0, math.pi / 3
 
 
 def splitmix64_reference_values():

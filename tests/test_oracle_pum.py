@@ -313,3 +313,20 @@ def test_galerkin_product_matches_dense_triple_product(small_biharmonic):
     # structural pattern of R A P equals the pattern read from the product of the patterns
     pat = bk.product_pattern(bk.product_pattern(h.P[1].transpose().pattern(), h.A[1].pattern()), h.P[1].pattern())
     assert pat == h.A[2].pattern()
+
+
+def test_anisotropic_neighbourhood_figure_fixture():
+    """The printed average neighbourhoods of Example 5.2 (tests/golden/aniso_neighbourhoods.json)
+    read as 0.5 x the fraction of rows of F^T S^-1 F containing an offset: the centre is 0.5,
+    offsets that every interior row has lose exactly the boundary rows (127/128 per direction at
+    level 7), and the figure is point-symmetric (F^T S^-1 F is symmetric)."""
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "aniso_neighbourhoods.json")))
+    m = 128
+    for name, op in g["opacity"].items():
+        assert op["0,0"] == 0.5
+        for key in ("0,1", "1,0", "0,-1", "-1,0"):
+            assert op[key] == pytest.approx(0.5 * (m - 1) / m, abs=5e-6)
+        for key, v in op.items():
+            dx, dy = (int(t) for t in key.split(","))
+            assert op.get(f"{-dx},{-dy}") == v, (name, key)
+            assert v <= 0.5 * (m - abs(dx)) * (m - abs(dy)) / m ** 2 + 5e-6
