@@ -295,6 +295,8 @@ pum_status pum_create(pum_ctx** out, int device, void* cuda_stream) {
     ctx->graphs = !(ng && ng[0] == '1');
     const char* ns = getenv("PUM_NO_SELL");
     ctx->sell = !(ns && ns[0] == '1');
+    const char* np = getenv("PUM_NO_PDL");
+    ctx->pdl = !(np && np[0] == '1');
     ctx->status = (DevStatus*)dalloc(sizeof(DevStatus));
     ctx->scal = (double*)dalloc(sizeof(double) * kScalSlots);
     ctx->partials = (double*)dalloc(sizeof(double) * (1 << 16));

@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(256) k_bsr_mv(int n_brows, int stride, int lan
                                                 const int* __restrict__ ci, const MT* __restrict__ vals,
                                                 const XT* __restrict__ x, EpiArgs e) {
   using AT = typename AccOf<MT>::type;
+  pdl_wait();
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t tid = gtid / lanes;  // output unknown
   const int g = (int)(gtid - tid * lanes);
@@ -43,6 +44,7 @@ __global__ void __launch_bounds__(256) k_bsr_mv(int n_brows, int stride, int lan
       for (int q = 0; q < D; ++q) acc = fma(a[q], xv[q], acc);
     }
   }
+  pdl_release();
   for (int o = lanes >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, lanes);
   const bool leader = active && g == 0;
   if constexpr (EPI == EPI_DOT) {
@@ -93,8 +95,8 @@ static void launch_mv_epi(pum_ctx* ctx, const Bsr& M, const void* x, int epi, co
 #define PUM_MV_CASE(E)                                                                                            \
   case E:                                                                                                         \
     if constexpr ((EPIS >> E) & 1u)                                                                               \
-      k_bsr_mv<D, MT, XT, YT, X2T, E><<<grid, bs, 0, s>>>(M.n_brows, M.stride, lanes, M.row_ptr, M.col_idx, v, xv, \
-                                                          e);                                                     \
+      launch_cycle_kernel(ctx, k_bsr_mv<D, MT, XT, YT, X2T, E>, dim3(grid), dim3(bs), 0, M.n_brows, M.stride, lanes, \
+                          M.row_ptr, M.col_idx, v, xv, e);                                                        \
     break;
   switch (epi) {
     PUM_MV_CASE(EPI_SET)
@@ -175,6 +177,8 @@ void bsr_mv(pum_ctx* ctx, const Bsr& M, int vdt, const void* x, int epi, const E
 
 template <typename D_, typename S_>
 __global__ void k_convert(D_* __restrict__ d, const S_* __restrict__ s, int64_t n) {
+  pdl_wait();
+  pdl_release();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     d[i] = (D_)s[i];
 }
@@ -188,9 +192,11 @@ void convert_vec(pum_ctx* ctx, void* dst, int ddt, const void* src, int sdt, int
     return;
   }
   if (ddt == PUM_F32 && sdt == PUM_F64)
-    k_convert<<<elem_grid(n), 256, 0, ctx->stream>>>((float*)dst, (const double*)src, n);
+    launch_cycle_kernel(ctx, k_convert<float, double>, dim3(elem_grid(n)), dim3(256), 0, (float*)dst,
+                        (const double*)src, n);
   else if (ddt == PUM_F64 && sdt == PUM_F32)
-    k_convert<<<elem_grid(n), 256, 0, ctx->stream>>>((double*)dst, (const float*)src, n);
+    launch_cycle_kernel(ctx, k_convert<double, float>, dim3(elem_grid(n)), dim3(256), 0, (double*)dst,
+                        (const float*)src, n);
   else
     throw Error{PUM_ERR_UNSUPPORTED, "convert_vec: dtype pair"};
   count_launch(ctx);

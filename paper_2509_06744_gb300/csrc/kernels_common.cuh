@@ -6,6 +6,14 @@
 
 namespace pum {
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream serialization may
+// start while its predecessor in the stream is still running: pdl_wait() blocks until that
+// predecessor has completed and its writes are visible (every thread that touches memory the
+// predecessor writes, or that later kernels read through this one, passes it first), and
+// pdl_release() lets the successor start launching.  Both are no-ops for ordinary launches.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <typename T> struct AccOf { using type = float; };
 template <> struct AccOf<double> { using type = double; };
 template <> struct AccOf<float2> { using type = double; };  // double-float (hi, lo) matrix values

@@ -215,6 +215,7 @@ struct pum_ctx {
   std::vector<pum::TimedEvent>* capture_ev = nullptr;  // set while a graph is being captured
   bool graphs = true;                                   // capture the V-cycle when the stream allows it
   bool sell = true;                                     // sliced layouts on large levels
+  bool pdl = true;                                      // programmatic dependent launch of the cycle's kernels
 };
 
 namespace pum {
@@ -269,6 +270,23 @@ void vcycle_level(pum_ctx* ctx, pum_hier* h, int l);
 void coarse_solve(pum_ctx* ctx, pum_hier* h, const void* b, void* x, int vdt);
 
 inline void count_launch(pum_ctx* ctx) { ctx->launches++; }
+
+// Launch a kernel of the V-cycle on the context's stream, with programmatic stream serialization
+// when enabled (the kernel must call pdl_wait() before touching dependent memory).
+template <typename... KArgs, typename... Args>
+void launch_cycle_kernel(pum_ctx* ctx, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = ctx->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = ctx->pdl ? 1 : 0;
+  PUM_CUDA(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
+}
 void timing_begin(pum_ctx* ctx, int tk);
 void timing_end(pum_ctx* ctx, int tk);
 // Collect the kernel times of the last timed graph replay (waits for it).

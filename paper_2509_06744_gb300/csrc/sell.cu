@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(kSellMaxThreads) k_sell_mv(int n_brows, int R,
   AT acc = 0;
   float sh = 0.f, sl = 0.f, sc = 0.f;  // double-float accumulator (kDF)
   XV xn[D];
+  pdl_wait();  // x and the epilogue's vectors come from the preceding kernel (the matrix does not)
   auto load_x = [&](int c, XV(&out)[D]) {
     if constexpr (kDF)
       load_row_df<D>(reinterpret_cast<const float2*>(x) + (int64_t)c * D, out);
@@ -203,6 +204,7 @@ __global__ void __launch_bounds__(kSellMaxThreads) k_sell_mv(int n_brows, int R,
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(empty + k);
   }
+  pdl_release();
   const int row = g * R + j;
   if (!(computes && row < n_brows)) return;
   if constexpr (kDF) {
@@ -232,14 +234,14 @@ static void sell_launch(pum_ctx* ctx, const Sell& S, int n_brows, const void* x,
   const size_t smem = sell_smem(S, D, sizeof(MT));
   const MT* v = (const MT*)S.vals;
   const XT* xv = (const XT*)x;
-  cudaStream_t s = ctx->stream;
   switch (epi) {
 #define PUM_SELL_CASE(E)                                                                                    \
   case E: {                                                                                                 \
     auto kern = k_sell_mv<D, MT, XT, YT, X2T, E>;                                                           \
     if (smem > 48 * 1024)                                                                                   \
       PUM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));        \
-    kern<<<S.n_groups, threads, smem, s>>>(n_brows, S.R, NS, S.goff, S.cols, v, xv, e, ctx->status);         \
+    launch_cycle_kernel(ctx, kern, dim3(S.n_groups), dim3(threads), smem, n_brows, S.R, NS, S.goff, S.cols, v, \
+                        xv, e, ctx->status);                                                                \
     break;                                                                                                  \
   }
     PUM_SELL_CASE(EPI_SET)

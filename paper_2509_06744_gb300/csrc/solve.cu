@@ -3,7 +3,7 @@
 // transfers and a dense coarsest solve (Section 5), and the outer FP64 PCG.
 #include <cmath>
 
-#include "pum_internal.cuh"
+#include "kernels_common.cuh"
 
 namespace pum {
 
@@ -117,6 +117,8 @@ void cheb4(pum_ctx* ctx, pum_hier* h, int l, const void* rhs, void* x, bool x_ze
 template <typename VT>
 __global__ void k_coarse_solve(const double* __restrict__ L, int N, const VT* __restrict__ b, VT* __restrict__ x) {
   extern __shared__ double y[];
+  pdl_wait();
+  pdl_release();
   for (int i = threadIdx.x; i < N; i += blockDim.x) y[i] = (double)b[i];
   __syncthreads();
   for (int i = 0; i < N; ++i) {  // L y = b
@@ -140,9 +142,11 @@ void coarse_solve(pum_ctx* ctx, pum_hier* h, const void* b, void* x, int vdt) {
   const int N = h->coarse.N;
   const size_t smem = sizeof(double) * N;
   if (vdt == PUM_F64)
-    k_coarse_solve<double><<<1, 256, smem, ctx->stream>>>(h->coarse.L, N, (const double*)b, (double*)x);
+    launch_cycle_kernel(ctx, k_coarse_solve<double>, dim3(1), dim3(256), smem, (const double*)h->coarse.L, N,
+                        (const double*)b, (double*)x);
   else
-    k_coarse_solve<float><<<1, 256, smem, ctx->stream>>>(h->coarse.L, N, (const float*)b, (float*)x);
+    launch_cycle_kernel(ctx, k_coarse_solve<float>, dim3(1), dim3(256), smem, (const double*)h->coarse.L, N,
+                        (const float*)b, (float*)x);
   count_launch(ctx);
   PUM_CUDA(cudaGetLastError());
 }
