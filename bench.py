@@ -224,8 +224,50 @@ def measure_variants(H, pr, b, stream, steps):
             torch.cuda.synchronize()
             out["v2k0_bicgstab"] = {"ms_per_solve": ev0.elapsed_time(ev1) / steps, "iters": rep["iters"],
                                     "cycles_per_solve": 2 * rep["iters"], "solves": steps}
-    out["anisotropic"] = measure_anisotropic(H.ctx, pr, stream, steps)
+    for name, fn in (("anisotropic", lambda: measure_anisotropic(H.ctx, pr, stream, steps)),
+                     ("batch", lambda: measure_batch(H.ctx))):
+        try:
+            out[name] = fn()
+        except Exception as ex:  # noqa: BLE001
+            out[name] = {"error": f"{type(ex).__name__}: {ex}"}
     return out
+
+
+def measure_batch(ctx, n_workers: int = 16, rhs: int = 16):
+    """The batched uneven workload: 64 biharmonic instances (sides 32/64/96/128, p = 2 or 3, drawn
+    by seed 3), adaptive FSAI (t_max = 6), FP32 form, 16 N(0,1) right-hand sides each: 1024 PCG
+    solves to 1e-8, run concurrently by 16 worker contexts and, for comparison, by one."""
+    import torch
+    import paper_2509_06744_gb300 as pum
+    insts = pin.batch_instances()
+    workers = pum.make_workers(n_workers)
+    t0 = time.perf_counter()
+    Hs = [pum.Hierarchy.assemble(ctx, 4, it.p, it.m, it.n_levels, f_coef=pin.fourier_coefficients(3),
+                                 nitsche=pin.NITSCHE_CONSTANTS[4]) for it in insts]
+    pum.setup_batch(workers, Hs, p0="lower", adaptive=True, t_max=6, k=3, smooth="f32", g="f32")
+    t_setup = time.perf_counter() - t0
+    items = []
+    for i, (H, it) in enumerate(zip(Hs, insts)):
+        for r in range(rhs):
+            b = torch.tensor(pin.normal_vector(it.n_dofs, 1000 * i + r), device="cuda")
+            items.append((H, b, torch.zeros_like(b)))
+    unknowns = sum(it.n_dofs for it in insts) * rhs
+    torch.cuda.synchronize()  # the workers' streams read what torch's stream wrote
+    res = {"instances": len(insts), "rhs_per_instance": rhs, "solves": len(items), "setup_s": t_setup}
+    for name, ws in (("concurrent", workers), ("one_worker", workers[:1])):
+        pum.solve_batch(ws, items[:len(insts)], rtol=RTOL, flexible=True)  # warm-up (graphs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = pum.solve_batch(ws, items, rtol=RTOL, flexible=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[name] = {"workers": len(ws), "s": dt, "solves_per_s": len(items) / dt,
+                     "unknown_solves_per_s": unknowns / dt, "max_iters": max(r["iters"] for r in reps)}
+    for H in Hs:
+        H.close()
+    for w in workers:
+        w.close()
+    return res
 
 
 def measure_anisotropic(ctx, pr, stream, steps):
@@ -399,7 +441,12 @@ def main():
                    "GBps": (ab[k] / (v[1] / v[0] * 1e-3) / 1e9) if v[0] else None,
                    "total_ms_per_solve": v[1] / args.steps} for k, v in kt.items()}
     dom = max(("resid", "g", "gt", "resid64"), key=lambda k: kt[k][1])
-    variants = measure_variants(H, pr, b, stream, max(3, args.steps // 4)) if not args.no_variants else None
+    variants = None
+    if not args.no_variants:
+        try:  # extra measurements: a failure there must not cost the headline line
+            variants = measure_variants(H, pr, b, stream, max(3, args.steps // 4))
+        except Exception as ex:  # noqa: BLE001
+            variants = {"error": f"{type(ex).__name__}: {ex}"}
 
     if rank != 0:
         return

@@ -227,6 +227,26 @@ pum_status bicgstab_solve(pum_ctx *ctx, pum_hier *h, const double *b, double *x,
  * double.  Synchronous. */
 pum_status pum_convergence_factor(pum_ctx *ctx, pum_hier *h, const double *e0, int n_cycles, double *rho);
 
+/* ---- batches of independent problems ---------------------------------------------------- */
+
+/* bfsai_setup of n distinct hierarchies with the same parameters, by n_workers host threads,
+ * thread w driving its own context workers[w] (distinct contexts on distinct streams).  status
+ * (n entries, may be NULL)
+ * receives each item's result; the return value is the first non-OK status in item order. */
+pum_status pum_setup_batch(pum_ctx *const *workers, int n_workers, pum_hier *const *hs, int n,
+                           const bfsai_params *fp, const smoother_params *sp, pum_status *status);
+
+/* n solves on independent problems: item i solves hs[i] x[i] = b[i] (device float64 vectors of
+ * that hierarchy's finest size) with pcg_solve (method 0) or bicgstab_solve (method 1), report
+ * in reps[i] (hist, rtol, maxit, flexible as for the single solve).  Items of the same hierarchy
+ * (several right-hand sides) run one after another on one worker; different hierarchies run
+ * concurrently, one per worker thread and context.  Worker contexts must be distinct and run on
+ * distinct streams (PUM_ERR_INVALID_ARG otherwise), and must not be used elsewhere during the
+ * call.  status and the return value as for pum_setup_batch. */
+pum_status pum_solve_batch(pum_ctx *const *workers, int n_workers, pum_hier *const *hs, int n,
+                           const double *const *b, double *const *x, pcg_report *reps, int method,
+                           pum_status *status);
+
 /* ---- single steps of the hot path (device float64 vectors) ------------------------ */
 
 /* r = b - A_level x (the residual of Algorithm 3). */

@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (PUM_BF16, PUM_F32, PUM_F64, PUM_MAT_A, PUM_MAT_A1, PUM_MAT_F0, PUM_MAT_G, PUM_MAT_G1,
                    PUM_MAT_GT, PUM_MAT_P, PUM_P0_DIAG, PUM_P0_LOWER)
 
-__all__ = ["Context", "Hierarchy", "PumError", "PUM_F64", "PUM_F32", "PUM_BF16", "PUM_P0_LOWER", "PUM_P0_DIAG",
+__all__ = ["Context", "Hierarchy", "PumError", "make_workers", "setup_batch", "solve_batch", "PUM_F64", "PUM_F32", "PUM_BF16", "PUM_P0_LOWER", "PUM_P0_DIAG",
            "PUM_MAT_A", "PUM_MAT_P", "PUM_MAT_G", "PUM_MAT_GT", "PUM_MAT_F0", "PUM_MAT_G1", "PUM_MAT_A1"]
 
 _DT = {"f64": PUM_F64, "f32": PUM_F32, "bf16": PUM_BF16}
@@ -114,6 +114,69 @@ def _bsr_view(indptr, indices, blocks, n_cols):
     return v, (indptr, indices, blocks)
 
 
+def _setup_params(p0="lower", adaptive=False, t_max=0, tau=1.0, nested=False, tie_rel=1e-9, k=2, lanczos_its=100,
+                  lanczos_safety=1.01, lanczos_seed=0, smooth="f64", g=None, mixed_levels=64, fp32_levels=64,
+                  smoother="cheb4", cycle="vkk"):
+    fp = _lib.FsaiParams(PUM_P0_LOWER if p0 == "lower" else PUM_P0_DIAG, int(adaptive), t_max, tau, int(nested),
+                         tie_rel)
+    sp = _lib.SmootherParams(k, lanczos_its, lanczos_safety, lanczos_seed, _DT[smooth], _DT[g or smooth],
+                             int(mixed_levels), int(fp32_levels), _SMOOTHER[smoother], _CYCLE[cycle])
+    return fp, sp
+
+
+def make_workers(n: int, device: int = 0):
+    """n contexts on n new streams of `device`, for setup_batch / solve_batch (each batch worker
+    needs its own stream).  Synchronise torch's stream before handing them vectors it wrote."""
+    import torch
+    out = []
+    for _ in range(n):
+        s = torch.cuda.Stream(device)
+        c = Context(device, stream=s.cuda_stream)
+        c._torch_stream = s  # keep the stream alive with the context
+        out.append(c)
+    return out
+
+
+def setup_batch(workers, hierarchies, **setup_kwargs):
+    """bfsai_setup of distinct hierarchies concurrently, one host thread per worker Context."""
+    fp, sp = _setup_params(**setup_kwargs)
+    n = len(hierarchies)
+    wa = (C.c_void_p * len(workers))(*[w.h for w in workers])
+    ha = (C.c_void_p * n)(*[h.h for h in hierarchies])
+    st = (C.c_int32 * n)()
+    rc = workers[0].lib.pum_setup_batch(wa, len(workers), ha, n, C.byref(fp), C.byref(sp), st)
+    if rc != 0:
+        bad = next((i for i in range(n) if st[i] != 0), None)
+        if bad is None:
+            raise PumError(rc, "batch arguments (distinct hierarchies; workers on distinct streams)")
+        raise PumError(int(st[bad]), f"batch set-up of item {bad}")
+    return [int(v) for v in st]
+
+
+def solve_batch(workers, items, rtol: float = 1e-8, maxit: int = 200, flexible: bool = False,
+                method: str = "pcg", allow_noconv=False):
+    """items: [(Hierarchy, b, x), ...]; solves them concurrently on the workers' streams (items of
+    one hierarchy in order on one worker).  Returns one report dict per item."""
+    n = len(items)
+    wa = (C.c_void_p * len(workers))(*[w.h for w in workers])
+    ha = (C.c_void_p * n)(*[it[0].h for it in items])
+    ba = (C.c_void_p * n)(*[_vec(it[1], "b") for it in items])
+    xa = (C.c_void_p * n)(*[_vec(it[2], "x") for it in items])
+    hists = [(C.c_double * (maxit + 1))() for _ in range(n)]
+    reps = (_lib.PcgReport * n)()
+    for i in range(n):
+        reps[i] = _lib.PcgReport(rtol, maxit, int(flexible), hists[i], 0, 0, 0.0)
+    st = (C.c_int32 * n)()
+    rc = workers[0].lib.pum_solve_batch(wa, len(workers), ha, n, ba, xa, reps, {"pcg": 0, "bicgstab": 1}[method], st)
+    for i in range(n):
+        if not (st[i] == 0 or (allow_noconv and st[i] == _lib.PUM_ERR_NOCONV)):
+            raise PumError(st[i], f"batch item {i}")
+    if rc == _lib.PUM_ERR_INVALID_ARG:
+        raise PumError(rc, "batch arguments (workers need distinct contexts on distinct streams)")
+    return [{"iters": reps[i].iters, "converged": bool(reps[i].converged), "final_relres": reps[i].final_relres,
+             "history": [hists[i][j] for j in range(reps[i].iters + 1)]} for i in range(n)]
+
+
 class Hierarchy:
     """Level hierarchy {A_l, P_l, G_l, beta_l} owned by the library (pum_hier)."""
 
@@ -177,10 +240,8 @@ class Hierarchy:
               nested: bool = False, tie_rel: float = 1e-9, k: int = 2, lanczos_its: int = 100,
               lanczos_safety: float = 1.01, lanczos_seed: int = 0, smooth: str = "f64", g: str | None = None,
               mixed_levels: int = 64, fp32_levels: int = 64, smoother: str = "cheb4", cycle: str = "vkk"):
-        fp = _lib.FsaiParams(PUM_P0_LOWER if p0 == "lower" else PUM_P0_DIAG, int(adaptive), t_max, tau,
-                             int(nested), tie_rel)
-        sp = _lib.SmootherParams(k, lanczos_its, lanczos_safety, lanczos_seed, _DT[smooth], _DT[g or smooth],
-                                 int(mixed_levels), int(fp32_levels), _SMOOTHER[smoother], _CYCLE[cycle])
+        fp, sp = _setup_params(p0, adaptive, t_max, tau, nested, tie_rel, k, lanczos_its, lanczos_safety, lanczos_seed,
+                               smooth, g, mixed_levels, fp32_levels, smoother, cycle)
         self.ctx.check(self.lib.bfsai_setup(self.ctx.h, self.h, C.byref(fp), C.byref(sp)))
 
     def close(self):

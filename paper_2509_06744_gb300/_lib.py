@@ -71,6 +71,10 @@ _SIGNATURES = {
     "pcg_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, P(PcgReport)]),
     "bicgstab_solve": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, P(PcgReport)]),
     "pum_convergence_factor": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, P(c_double)]),
+    "pum_setup_batch": (c_int32, [P(c_void_p), c_int32, P(c_void_p), c_int32, P(FsaiParams), P(SmootherParams),
+                                  P(c_int32)]),
+    "pum_solve_batch": (c_int32, [P(c_void_p), c_int32, P(c_void_p), c_int32, P(c_void_p), P(c_void_p),
+                                  P(PcgReport), c_int32, P(c_int32)]),
     "pum_residual": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, c_void_p]),
     "pum_fsai_apply": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
     "pum_restrict": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),

@@ -372,6 +372,7 @@ pum_status pum_assemble(pum_ctx* ctx, const pum_problem* pr, pum_hier** out, dou
       C.d = F.d;
       galerkin(ctx, F, C);
     }
+    PUM_CUDA(cudaStreamSynchronize(ctx->stream));  // the hierarchy may next be used from another context
     return PUM_OK;
   });
   if (st != PUM_OK) {
@@ -413,6 +414,7 @@ pum_status pum_hier_from_bsr(pum_ctx* ctx, int n_levels, const pum_bsr_view* A, 
       L.m = (int)std::lround(std::sqrt((double)L.n));
       if (L.m * L.m != L.n) L.m = 0;
     }
+    PUM_CUDA(cudaStreamSynchronize(ctx->stream));  // the hierarchy may next be used from another context
     return PUM_OK;
   });
   if (st != PUM_OK) {
@@ -427,6 +429,7 @@ pum_status bfsai_setup(pum_ctx* ctx, pum_hier* h, const bfsai_params* fp, const 
   if (!ctx || !h) return PUM_ERR_INVALID_ARG;
   return guard(ctx, [&]() {
     check_params(fp, sp);
+    PUM_CUDA(cudaStreamSynchronize(ctx->stream));  // no queued kernel may still use what is freed next
     free_smoother(h);
     for (auto& L : h->lv)
       for (Bsr* m : {&L.G64, &L.F064, &L.G164, &L.A1}) bsr_free(*m);
@@ -764,6 +767,7 @@ pum_status pum_hier_load(pum_ctx* ctx, const char* path, pum_hier** out) {
 
 pum_status pum_hier_destroy(pum_hier* h) {
   if (!h) return PUM_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();  // kernels queued on any stream may still read the hierarchy
   graph_destroy(h->vgraph);
   for (auto& L : h->lv) free_level(L);
   for (auto& w : h->w64)

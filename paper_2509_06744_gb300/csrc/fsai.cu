@@ -408,7 +408,9 @@ void run_rows(pum_ctx* ctx, const Bsr& A, const Pattern& P, const std::vector<in
   PUM_CHECK(d <= kMaxD, PUM_ERR_UNSUPPORTED, "FSAI block size above 21");
   PUM_CHECK(max_cand <= 64 * 64, PUM_ERR_UNSUPPORTED, "too many FSAI candidates");
   const int s_max = max_np * d;
-  const int limit = max_smem_optin(ctx->device);
+  cudaFuncAttributes fa{};
+  PUM_CUDA(cudaFuncGetAttributes(&fa, (const void*)k_fsai_rows));
+  const int limit = max_smem_optin(ctx->device) - (int)fa.sharedSizeBytes;  // dynamic part
   int group = 1;  // the kernel lays shared memory out with at least one candidate group
   if (crp) {
     group = std::min(std::max(max_cand, 1), 64);
@@ -417,7 +419,9 @@ void run_rows(pum_ctx* ctx, const Bsr& A, const Pattern& P, const std::vector<in
   const size_t smem = fsai_smem_bytes(s_max, d, group, max_np, max_cand);
   PUM_CHECK(smem <= (size_t)limit, PUM_ERR_UNSUPPORTED,
             "FSAI row too large for shared memory (s = " + std::to_string(s_max) + ")");
-  PUM_CUDA(cudaFuncSetAttribute(k_fsai_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // the largest limit, not this launch's size: concurrent set-ups (batches) share the function
+  // attribute, and a smaller value set by another thread would fail this launch
+  allow_max_dynamic_smem((const void*)k_fsai_rows);
   int* dprp = dev_upload(prp, s);
   int* dpci = dev_upload(pci, s);
   int* drows = dev_upload(rows, s);
@@ -693,6 +697,9 @@ void lanczos_level(pum_ctx* ctx, pum_hier* h, int l) {
     Bsr tmp;
     bsr_convert(tmp, src64, gdt, s);
     bsr_widen(dst, tmp, s);
+    // tmp's memory must not be freed (and handed to another thread's allocation) while the
+    // widening kernel may still read it
+    PUM_CUDA(cudaStreamSynchronize(s));
     bsr_free(tmp);
   };
   if (nested) {

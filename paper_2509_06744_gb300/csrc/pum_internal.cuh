@@ -30,8 +30,10 @@ struct Error {
 #define PUM_CUDA(call)                                                                       \
   do {                                                                                       \
     cudaError_t e_ = (call);                                                                 \
-    if (e_ != cudaSuccess)                                                                   \
+    if (e_ != cudaSuccess) {                                                                 \
+      cudaGetLastError(); /* a non-sticky error must not resurface in a later check */       \
       throw ::pum::Error{PUM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};  \
+    }                                                                                        \
   } while (0)
 
 #define PUM_CHECK(cond, status, text)                                                        \
@@ -270,6 +272,18 @@ void vcycle_level(pum_ctx* ctx, pum_hier* h, int l);
 void coarse_solve(pum_ctx* ctx, pum_hier* h, const void* b, void* x, int vdt);
 
 inline void count_launch(pum_ctx* ctx) { ctx->launches++; }
+
+// Raise a kernel's dynamic shared memory limit to the most the device allows it (the opt-in
+// limit less its static shared memory).  Always the same value for a kernel, so threads that
+// launch it concurrently with different sizes cannot lower the limit under one another.
+inline void allow_max_dynamic_smem(const void* kern) {
+  int dev = 0, optin = 0;
+  PUM_CUDA(cudaGetDevice(&dev));
+  PUM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa{};
+  PUM_CUDA(cudaFuncGetAttributes(&fa, kern));
+  PUM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes));
+}
 
 // Launch a kernel of the V-cycle on the context's stream, with programmatic stream serialization
 // when enabled (the kernel must call pdl_wait() before touching dependent memory).

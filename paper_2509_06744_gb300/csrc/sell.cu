@@ -239,7 +239,7 @@ static void sell_launch(pum_ctx* ctx, const Sell& S, int n_brows, const void* x,
   case E: {                                                                                                 \
     auto kern = k_sell_mv<D, MT, XT, YT, X2T, E>;                                                           \
     if (smem > 48 * 1024)                                                                                   \
-      PUM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));        \
+      allow_max_dynamic_smem((const void*)kern);                                                           \
     launch_cycle_kernel(ctx, kern, dim3(S.n_groups), dim3(threads), smem, n_brows, S.R, NS, S.goff, S.cols, v, \
                         xv, e, ctx->status);                                                                \
     break;                                                                                                  \
@@ -363,7 +363,7 @@ static int sell_occupancy(int R, int max_slots) {
     kern = (const void*)k_sell_mv<D, MT, float2, float, double, EPI_RESID>;
   else
     kern = (const void*)k_sell_mv<D, MT, float, float, double, EPI_CHEB>;
-  if (smem > 48 * 1024) PUM_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > 48 * 1024) allow_max_dynamic_smem(kern);
   int nb = 0;
   PUM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem));
   return nb;

@@ -117,6 +117,36 @@ def anisotropy_tensor(kappa: float, theta: float) -> tuple:
 ANISO_KAPPA, ANISO_THETA = 10.0, math.pi / 3
 
 
+@dataclasses.dataclass(frozen=True)
+class Instance:
+    """One problem of the batched uneven workload: biharmonic, m x m patches, degree p, levels
+    halving m while it stays even (coarsest 1x1 or an odd side such as 3x3)."""
+    m: int
+    p: int
+
+    @property
+    def n_levels(self) -> int:
+        n, m = 1, self.m
+        while m % 2 == 0 and m > 1:
+            m //= 2
+            n += 1
+        return n
+
+    @property
+    def d(self) -> int:
+        return (self.p + 1) * (self.p + 2) // 2
+
+    @property
+    def n_dofs(self) -> int:
+        return self.d * self.m * self.m
+
+
+def batch_instances(seed: int = 3, count: int = 64, sides=(32, 64, 96, 128), degrees=(2, 3)) -> list:
+    """The batched workload: `count` biharmonic instances with sides and degrees drawn by `seed`."""
+    rs = np.random.default_rng(seed)
+    return [Instance(int(rs.choice(sides)), int(rs.choice(degrees))) for _ in range(count)]
+
+
 def splitmix64_reference_values():
     """First outputs of SplitMix64 seeded with 0 (Steele, Lea & Flood 2014), as published
     test values of the generator; both the oracle's and the library's implementations are

@@ -624,3 +624,43 @@ def test_kernel_timing_counts_every_finest_launch(lib, small_biharmonic, graph):
     assert kt["pcg_ap"][0] == rep["iters"] and all(v[1] > 0 for v in kt.values())
     # with only the G^T class selected, the other classes record nothing
     assert kt_gt["gt"][0] == kt["gt"][0] and all(kt_gt[n][0] == 0 for n in ("resid", "g", "pcg_ap", "resid64"))
+
+
+# --------------------------------------------- batched independent problems
+
+def test_batch_setup_and_solves_match_single_calls(lib):
+    """Uneven instances (sides 8, 12 (3x3 coarsest), 16; degrees 2 and 3), three right-hand sides
+    each, set up and solved concurrently by three worker contexts: every solve is bit for bit the
+    single-call solve, and one instance matches the oracle's PCG history."""
+    import torch
+    insts = [pin.Instance(8, 2), pin.Instance(12, 3), pin.Instance(16, 3), pin.Instance(16, 2)]
+    home = lib.Context(0)
+    workers = lib.make_workers(3)
+    with pytest.raises(lib.PumError):  # workers sharing a stream are refused
+        lib.solve_batch([home, lib.Context(0)], [], rtol=1e-8)
+    coef = pin.fourier_coefficients(7)
+    Hs = [lib.Hierarchy.assemble(home, 4, it.p, it.m, it.n_levels, f_coef=coef, nitsche=pin.NITSCHE_CONSTANTS[4])
+          for it in insts]
+    kw = dict(p0="lower", adaptive=True, t_max=3, k=3)
+    assert lib.setup_batch(workers, Hs, **kw) == [0] * len(Hs)
+    items = []
+    for H, it in zip(Hs, insts):
+        for r in range(3):
+            items.append((H, cuda(pin.normal_vector(it.n_dofs, 200 + r)), cuda(np.zeros(it.n_dofs))))
+    torch.cuda.synchronize()  # the workers' streams read what torch's stream wrote
+    reps = lib.solve_batch(workers, items, rtol=1e-8, maxit=100)
+    for (H, b, x), rep in zip(items, reps):
+        x1 = torch.zeros_like(b)
+        rep1 = H.pcg(b, x1, rtol=1e-8, maxit=100)
+        assert rep["converged"] and rep["iters"] == rep1["iters"] and rep["history"] == rep1["history"]
+        assert torch.equal(x, x1)
+    it = insts[1]
+    h = pum.build_hierarchy(it.m, it.p, 4, it.n_levels, f=pum.fourier_source(coef, 2.0),
+                            constants=pin.NITSCHE_CONSTANTS[4])
+    ref = solver.build_setup(h, k=3, mode="adaptive", P0="lower", t_max=3)
+    bh = pin.normal_vector(it.n_dofs, 200)
+    res = solver.solve(ref, bh, rtol=1e-8)
+    assert reps[3]["iters"] == res.iters
+    assert np.max(np.abs(np.array(reps[3]["history"]) - np.array(res.history))) <= TOL_HISTORY
+    for H in Hs:
+        H.close()

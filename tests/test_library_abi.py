@@ -50,6 +50,10 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.pum_launch_count(None) == 0
     n = C.c_int32()
     assert lib.pum_hier_levels(None, C.byref(n)) == _lib.PUM_ERR_INVALID_ARG
+    # batches validate their arrays before any device work
+    assert lib.pum_solve_batch(None, 1, None, 1, None, None, None, 0, None) == _lib.PUM_ERR_INVALID_ARG
+    fp, sp = _lib.FsaiParams(), _lib.SmootherParams()
+    assert lib.pum_setup_batch(None, 0, None, 0, C.byref(fp), C.byref(sp), None) == _lib.PUM_ERR_INVALID_ARG
 
 
 def test_missing_device_is_an_error_not_a_fallback(lib):
