@@ -302,6 +302,7 @@ pum_status pum_create(pum_ctx** out, int device, void* cuda_stream) {
     ctx->partials = (double*)dalloc(sizeof(double) * (1 << 16));
     PUM_CUDA(cudaMemset(ctx->status, 0, sizeof(DevStatus)));
     PUM_CUDA(cudaMemset(ctx->scal, 0, sizeof(double) * kScalSlots));
+    PUM_CUDA(cudaStreamSynchronize(0));  // legacy-stream memsets, before the context's own stream runs
     PUM_CUDA(cudaMallocHost(&ctx->h_scal, sizeof(double) * kScalSlots));
     return PUM_OK;
   });
@@ -339,7 +340,7 @@ pum_status pum_sync(pum_ctx* ctx) {
     DevStatus st{};
     PUM_CUDA(cudaMemcpy(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost));
     if (st.code) {
-      PUM_CUDA(cudaMemset(ctx->status, 0, sizeof(DevStatus)));
+      PUM_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), ctx->stream));
       throw Error{(pum_status)st.code, "device status " + std::to_string(st.code) + " at row " + std::to_string(st.info)};
     }
     return PUM_OK;

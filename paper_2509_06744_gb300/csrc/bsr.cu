@@ -292,7 +292,11 @@ void bsr_alloc(Bsr& m, int n_brows, int n_bcols, int d, int dt, const std::vecto
   }
   PUM_CUDA(cudaMemcpy(m.row_ptr, rp.data(), sizeof(int) * rp.size(), cudaMemcpyHostToDevice));
   if (!ci.empty()) PUM_CUDA(cudaMemcpy(m.col_idx, ci.data(), sizeof(int) * ci.size(), cudaMemcpyHostToDevice));
+  // cudaMemset runs on the legacy stream, which does not order with the non-blocking streams the
+  // library works on: wait for it, or a kernel on such a stream could write the values first
+  // and be zeroed after (seen with concurrent set-ups)
   PUM_CUDA(cudaMemset(m.vals, 0, dt_size(dt) * (size_t)m.stride * std::max<int64_t>(m.nnzb, 1)));
+  PUM_CUDA(cudaStreamSynchronize(0));
 }
 
 template <typename DT, typename ST>

@@ -383,7 +383,7 @@ void check_status(pum_ctx* ctx, const char* what) {
   DevStatus st{};
   PUM_CUDA(cudaMemcpy(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost));
   if (st.code != 0) {
-    PUM_CUDA(cudaMemset(ctx->status, 0, sizeof(DevStatus)));
+    PUM_CUDA(cudaMemsetAsync(ctx->status, 0, sizeof(DevStatus), ctx->stream));
     const char* stage = st.where == kWhereFsai ? "Cholesky of A[P~,P~] or S_kk" :
                         st.where == kWhereAdaptive ? "candidate Schur complement" : "dense Cholesky";
     throw Error{(pum_status)st.code, std::string(what) + ": factorisation failed (non-positive pivot, " + stage +
