@@ -47,19 +47,38 @@ def algorithmic_bytes(info, smooth_bytes, g_bytes, vec_bytes, iterate_bytes):
     the smoother's epilogue accumulates into)."""
     d = info["d"]
     N = info["n"] * d
-    return {
+    G = info["nnzb_G"] * (d * d * g_bytes + 4)
+    out = {
         "resid": info["nnzb_A"] * (d * d * smooth_bytes + 4) + 3 * N * vec_bytes,   # e, b read; r write
-        "g": info["nnzb_G"] * (d * d * g_bytes + 4) + 2 * N * vec_bytes,             # r read; t write
-        # t, p, e read; p, e write; iterate read + write
-        "gt": info["nnzb_G"] * (d * d * g_bytes + 4) + 5 * N * vec_bytes + 2 * N * iterate_bytes,
         "pcg_ap": info["nnzb_A"] * (d * d * 8 + 4) + 2 * N * 8,                        # A (FP64), p read; q write
         # FP64 A on the FP64 iterate and right-hand side, FP32 result
         "resid64": info["nnzb_A"] * (d * d * 8 + 4) + 2 * N * iterate_bytes + N * vec_bytes,
     }
+    if info.get("fused_fsai"):
+        # G read once: values and columns, r read, partial products G_ji^T t_j written (d FP32 per block)
+        out["g"] = G + N * vec_bytes + info["nnzb_G"] * d * 4
+        # partial products and their int32 slot positions read; p, e read and written; iterate read + write
+        out["gt"] = info["nnzb_G"] * (d * 4 + 4) + 4 * N * vec_bytes + 2 * N * iterate_bytes
+    else:
+        out["g"] = G + 2 * N * vec_bytes                                                # r read; t write
+        # t, p, e read; p, e write; iterate read + write
+        out["gt"] = G + 5 * N * vec_bytes + 2 * N * iterate_bytes
+    return out
 
 
-def profiled_traffic(profile="profiles/cheb4_gt_sell_biharmonic256.md",
-                     sources=("paper_2509_06744_gb300/csrc/sell.cu", "paper_2509_06744_gb300/csrc/kernels_common.cuh")):
+ROOFLINE = {  # roofline kernel per FSAI form: class, description, ncu summary, sources it was taken from
+    True: ("g", "g: fused FSAI partial products G_ji^T t_j (G read once), finest level, FP32",
+           "profiles/fsai_fused_partial_biharmonic256.md",
+           ("paper_2509_06744_gb300/csrc/gg.cu", "paper_2509_06744_gb300/csrc/bulk.cuh",
+            "paper_2509_06744_gb300/csrc/kernels_common.cuh")),
+    False: ("gt", "gt: G^T t + Chebyshev-4 update, finest level, FP32",
+            "profiles/cheb4_gt_sell_biharmonic256.md",
+            ("paper_2509_06744_gb300/csrc/sell.cu", "paper_2509_06744_gb300/csrc/bulk.cuh",
+             "paper_2509_06744_gb300/csrc/kernels_common.cuh")),
+}
+
+
+def profiled_traffic(profile, sources):
     """DRAM bytes per launch of the roofline kernel from its committed ncu summary, or None when
     the kernel sources have changed since that capture (the summary records their hash)."""
     import hashlib
@@ -377,8 +396,10 @@ def main():
     # headline form: FP32 smoothing with FP64 iterates and residuals, FP64 PCG
     H.setup(p0=pr.fsai_p0, adaptive=pr.adaptive, t_max=pr.t_max, tau=pr.tau, k=pr.cheb_k, smooth="f32", g="f32")
     timed_solves(args.warmup, True)
-    # timed region: events around the roofline kernel class only (G^T product + Chebyshev update)
-    ctx.timing(True, ["gt"])
+    # timed region: events around the roofline kernel class only
+    info = H.info(0)
+    roof_tk, roof_desc, roof_profile, roof_sources = ROOFLINE[bool(info["fused_fsai"])]
+    ctx.timing(True, [roof_tk])
     ctx.timing_reset()
     launches0 = ctx.launches
     if world > 1:
@@ -430,13 +451,12 @@ def main():
             e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = statistics.median(e2e)
 
-    # roofline of the Chebyshev G^T kernel (the finest-level class with the largest total time),
-    # its launch durations taken live over the timed region
-    info = H.info(0)
+    # roofline of the FSAI kernel that streams G (the finest-level class with the largest total
+    # time), its launch durations taken live over the timed region
     ab = algorithmic_bytes(info, 4, 4, 4, 8)
     peak, peak_kind = load_peaks()
-    n_l, ms_l = kt_live["gt"]
-    achieved = ab["gt"] / (ms_l / n_l * 1e-3) / 1e9
+    n_l, ms_l = kt_live[roof_tk]
+    achieved = ab[roof_tk] / (ms_l / n_l * 1e-3) / 1e9
     kernels = {k: {"launches": v[0], "avg_us": (v[1] / v[0] * 1e3) if v[0] else None,
                    "GBps": (ab[k] / (v[1] / v[0] * 1e-3) / 1e9) if v[0] else None,
                    "total_ms_per_solve": v[1] / args.steps} for k, v in kt.items()}
@@ -466,10 +486,10 @@ def main():
         "fp64_plain": {"ms_per_solve": plain_ms, "pcg_iters": plain_iters, "dtype": "f64"},
         "setup_s": {"assembly_and_galerkin": t_asm, "fsai_lanczos_fp64": t_fsai},
         "kernels_finest": kernels,
-        "roofline": {"kernel": "gt: G^T t + Chebyshev-4 update, finest level, FP32", "bound": "hbm",
+        "roofline": {"kernel": roof_desc, "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": profiled_traffic(),
-                     "peak_source": peak_kind, "algorithmic_bytes_per_launch": ab["gt"], "launches_timed": n_l,
+                     "traffic": profiled_traffic(roof_profile, roof_sources),
+                     "peak_source": peak_kind, "algorithmic_bytes_per_launch": ab[roof_tk], "launches_timed": n_l,
                      "largest_total_class": dom},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},

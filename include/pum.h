@@ -152,6 +152,9 @@ typedef struct {
   int32_t coarsest;
   int32_t nested_inner; /* nested set-up: 1 inner FSAI of A1 = F0 A F0^T; 0 inner block Jacobi
                            (used when A1 is not numerically SPD in FP64; equals plain FSAI)  */
+  int32_t fused_fsai;   /* 1: this level applies G^T G (nested: G1^T G1) reading G once --
+                           partial products G_ji^T t_j, then a fixed-order gather (sliced FP32
+                           levels; environment PUM_NO_FUSED_FSAI=1 at pum_create turns it off) */
 } pum_level_info;
 
 /* Matrices selectable in pum_hier_export. */

@@ -54,7 +54,8 @@ class PcgReport(C.Structure):
 class LevelInfo(C.Structure):
     _fields_ = [("m", c_int32), ("n", c_int32), ("d", c_int32), ("nnzb_A", c_int64), ("nnzb_G", c_int64),
                 ("nnzb_GT", c_int64), ("nnzb_P", c_int64), ("nnzb_F0", c_int64), ("nnzb_G1", c_int64),
-                ("beta", c_double), ("logdet_S", c_double), ("coarsest", c_int32), ("nested_inner", c_int32)]
+                ("beta", c_double), ("logdet_S", c_double), ("coarsest", c_int32), ("nested_inner", c_int32),
+                ("fused_fsai", c_int32)]
 
 
 P = C.POINTER

@@ -71,6 +71,7 @@ void free_level(Level& L) {
     if (*v) { cudaFree(*v); *v = nullptr; }
   sell_free(L.Adf);
   sell_free(L.Pdf);
+  gg_free(L.gg);
 }
 
 void free_smoother(pum_hier* h) {
@@ -81,6 +82,7 @@ void free_smoother(pum_hier* h) {
       if (*v) { cudaFree(*v); *v = nullptr; }
     sell_free(L.Adf);
     sell_free(L.Pdf);
+    gg_free(L.gg);
   }
   for (auto& w : h->w64)
     if (w) { cudaFree(w); w = nullptr; }
@@ -161,9 +163,16 @@ void finalize_smoother(pum_ctx* ctx, pum_hier* h) {
       }
     }
     if (vdt == PUM_F32) bsr_convert(L.As, L.A, PUM_F32, s);
-    if (vdt == PUM_F32 && h->sell)
+    if (vdt == PUM_F32 && h->sell) {
+      // The factor next to the Chebyshev update's input (G, or the inner G1 of the nested chain)
+      // is applied through the fused layout when it fits; its two sliced copies are then unused.
+      Bsr* fg = h->fp.nested ? &L.G1 : &L.G;
+      Bsr* fgt = h->fp.nested ? &L.G1T : &L.GT;
+      if (h->fused_fsai && !fg->empty() && fg->n_brows >= kSellMinRows) gg_build(L.gg, *fg, s, ctx->sm_count);
       for (Bsr* m : {&L.As, &L.G, &L.GT, &L.F0, &L.F0T, &L.G1, &L.G1T, &L.Ps, &L.PTs})
-        if (!m->empty() && m->n_brows >= kSellMinRows) sell_build(*m, s, ctx->sm_count);
+        if (!m->empty() && m->n_brows >= kSellMinRows && !(L.gg.S.R > 0 && (m == fg || m == fgt)))
+          sell_build(*m, s, ctx->sm_count);
+    }
     for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e}) *v = dalloc(vs * N);
     if (h->smooth_dt == PUM_F32 && l > 0 && (l < h->sp.mixed_levels || l == nl - 1)) {
       L.b64 = (double*)dalloc(sizeof(double) * N);
@@ -297,6 +306,8 @@ pum_status pum_create(pum_ctx** out, int device, void* cuda_stream) {
     ctx->sell = !(ns && ns[0] == '1');
     const char* np = getenv("PUM_NO_PDL");
     ctx->pdl = !(np && np[0] == '1');
+    const char* nf = getenv("PUM_NO_FUSED_FSAI");
+    ctx->fused_fsai = !(nf && nf[0] == '1');
     ctx->status = (DevStatus*)dalloc(sizeof(DevStatus));
     ctx->scal = (double*)dalloc(sizeof(double) * kScalSlots);
     ctx->partials = (double*)dalloc(sizeof(double) * (1 << 16));
@@ -439,6 +450,7 @@ pum_status bfsai_setup(pum_ctx* ctx, pum_hier* h, const bfsai_params* fp, const 
     h->smooth_dt = sp->smooth_dt;
     h->g_dt = sp->g_dt;
     h->sell = ctx->sell;
+    h->fused_fsai = ctx->fused_fsai;
     const int nl = (int)h->lv.size();
     PUM_CHECK(h->lv.back().n * h->lv.back().d <= 4096, PUM_ERR_UNSUPPORTED, "coarsest level above 4096 unknowns");
     PUM_CHECK(sp->smooth_dt == PUM_F64 || sp->fp32_levels >= nl || sp->fp32_levels <= sp->mixed_levels,
@@ -629,6 +641,7 @@ pum_status pum_level_info_get(const pum_hier* h, int level, pum_level_info* info
   info->logdet_S = L.logdet_S;
   info->coarsest = level == (int)h->lv.size() - 1;
   info->nested_inner = L.nested_inner;
+  info->fused_fsai = L.gg.S.R > 0 ? 1 : 0;
   return PUM_OK;
 }
 
@@ -728,6 +741,7 @@ pum_status pum_hier_load(pum_ctx* ctx, const char* path, pum_hier** out) {
       h->smooth_dt = h->sp.smooth_dt;
       h->g_dt = h->sp.g_dt;
       h->sell = ctx->sell;
+      h->fused_fsai = ctx->fused_fsai;
       int32_t nl;
       rd(f, &nl, sizeof(nl));
       PUM_CHECK(nl >= 1 && nl <= 16, PUM_ERR_IO, "corrupt level count");

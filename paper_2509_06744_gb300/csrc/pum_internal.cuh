@@ -48,7 +48,7 @@ struct DevStatus {
   int where;  // which kernel family (see kWhere*)
   int pad;
 };
-enum { kWhereFsai = 1, kWhereCoarse = 2, kWhereAdaptive = 3, kWhereLanczos = 4, kWhereSell = 5 };
+enum { kWhereFsai = 1, kWhereCoarse = 2, kWhereAdaptive = 3, kWhereLanczos = 4, kWhereSell = 5, kWhereGg = 6 };
 
 __device__ inline void set_status(DevStatus* s, int code, int info, int where) {
   if (atomicCAS(&s->code, 0, code) == 0) {
@@ -91,6 +91,21 @@ struct Bsr {
 };
 
 void bsr_free(Bsr& m);
+// Block-FSAI application z = G^T (G r) that reads G once (gg.cu): G in the sliced layout with
+// groups small enough to stay whole in shared memory, and the partial products G_ji^T t_j
+// (d floats per block) stored in the block order of G^T.
+struct FusedG {
+  Sell S;
+  int n = 0, d = 0, dt = PUM_F32;  // block rows, block size, value type of G
+  int ctas = 0;   // persistent CTAs of the partial-product kernel
+  int parts = 1;  // its consumer partitions of a group's slots
+  int* tptr = nullptr;  // n + 1 offsets of the block rows of G^T (blocks (i, j), ascending j)
+  int* tpos = nullptr;  // per slot entry of S (slot * R + row in group): position of that block
+                        // of G in G^T's block order, -1 for padding
+  float* w = nullptr;   // nnzb(G) * d partial products, G^T's block order
+};
+void gg_build(FusedG& F, const Bsr& G, cudaStream_t s, int sm_count);
+void gg_free(FusedG& F);
 // Sliced layout (sell.cu): build for a FP32/BF16 matrix; product through it (false: not applicable).
 void sell_build(Bsr& m, cudaStream_t s, int sm_count);
 void sell_free(Sell& s);
@@ -103,6 +118,10 @@ int level_gdt(const pum_hier* h, int l);
 // product with a split vector (float2 hi, lo per unknown) in double-float arithmetic: RESID
 // into an FP32 y with an FP64 b, or ADD into an FP64 y.
 void sell_build_df(Sell& S, const Bsr& M64, cudaStream_t s, int sm_count);
+// Largest group size R of a sliced layout for block size d.
+int sell_rows_max(int d);
+// Sliced layout with a given group size R (FP32 or BF16 values).
+void sell_build_rows(Sell& S, const Bsr& M, int R, cudaStream_t s);
 void sell_df_mv(pum_ctx* ctx, const Sell& S, int d, int n_brows, const void* xs, int epi, const struct EpiArgs& e,
                 int tk = -1);
 constexpr int kSellMinRows = 4096;  // levels with at least this many block rows use it (groups of
@@ -153,6 +172,7 @@ struct Level {
   Sell Adf;
   void* zs = nullptr;
   Sell Pdf;  // P as FP32 pairs, when the coarser level is a mixed sliced level too
+  FusedG gg;  // G (or nested G1) read once per application, on sliced FP32 levels
 };
 
 struct Coarse {
@@ -195,6 +215,7 @@ struct pum_hier {
   double* wb[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   pum::GraphCache vgraph;  // captured V-cycle
   bool sell = true;        // sliced layouts for the large levels' FP32 products
+  bool fused_fsai = true;  // G read once per FSAI application on those levels
 };
 
 struct pum_ctx {
@@ -218,6 +239,7 @@ struct pum_ctx {
   bool graphs = true;                                   // capture the V-cycle when the stream allows it
   bool sell = true;                                     // sliced layouts on large levels
   bool pdl = true;                                      // programmatic dependent launch of the cycle's kernels
+  bool fused_fsai = true;                               // G read once per FSAI application on sliced levels
 };
 
 namespace pum {
@@ -247,6 +269,8 @@ struct EpiArgs {
 
 // y (by epilogue) = M x for a BSR matrix; vector dtype vdt (F64 or F32).
 void bsr_mv(pum_ctx* ctx, const Bsr& M, int vdt, const void* x, int epi, const EpiArgs& e, int tk = -1);
+// z (by epilogue) = G^T (G r) through the fused layout (FP32 vectors); timing classes of its two kernels.
+void gg_apply(pum_ctx* ctx, const FusedG& F, const void* r, int epi, const EpiArgs& e, int tk_g = -1, int tk_gt = -1);
 void convert_vec(pum_ctx* ctx, void* dst, int ddt, const void* src, int sdt, int64_t n);
 void zero_vec(pum_ctx* ctx, void* dst, int dt, int64_t n);
 

@@ -14,67 +14,25 @@
 // sum_c A_j[r][c] x[col d + c] over the slots, loading the next slot's x segment while the
 // current chunk lands.  The bytes in flight per SM are then set by shared memory, not by
 // registers.  Every wait is bounded: on expiry the kernel records PUM_ERR_TIMEOUT in the
-// context's status word, drains its own copies (bounded) and returns.  Padding slots read
+// context's status word, drains its own copies (bounded) and returns.  The chunks are copied with
+// an evict-first L2 policy: each is read once per product, and the vectors the next kernels
+// read should stay in L2 instead.  Padding slots read
 // column 0 against zero values, which keeps the loop branch-free.  The fused epilogues are those
 // of the block-row kernel.
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
 
+#include "bulk.cuh"
 #include "kernels_common.cuh"
 
 namespace pum {
 
 namespace {
 
-constexpr int kWaitLimit = 1 << 22;  // polls of an mbarrier before a wait gives up
 constexpr int kHeader = 128;         // bytes for the full/empty barriers of up to 8 stages
 constexpr int kMaxStages = 8;
 constexpr int kSellMaxThreads = 32 + 352;  // producer warp + the largest consumer group (d = 21, R = 16)
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for the phase of the given parity to complete; false if it did not within the limit.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int i = 0; i < kWaitLimit; ++i)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-
-// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to this
-// CTA's shared memory, completing on `bar` as transaction bytes.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
 
 }  // namespace
 
@@ -138,9 +96,10 @@ __global__ void __launch_bounds__(kSellMaxThreads) k_sell_mv(int n_brows, int R,
       mbar_init(empty + k, (uint32_t)n_consumer_warps);
     }
     mbar_fence_init();
+    const uint64_t pol = l2_evict_first_policy();
     for (int s = 0; s < min(NS, ns); ++s) {
       mbar_expect_tx(full + s, chunk);
-      bulk_g2s(stage + (size_t)s * chunk_elems, src + (int64_t)s * chunk_elems, chunk, full + s);
+      bulk_g2s_policy(stage + (size_t)s * chunk_elems, src + (int64_t)s * chunk_elems, chunk, full + s, pol);
     }
   }
   for (int i = threadIdx.x; i < ns * R; i += blockDim.x) scol[i] = max(__ldg(cols + (int64_t)s0 * R + i), 0);
@@ -150,6 +109,7 @@ __global__ void __launch_bounds__(kSellMaxThreads) k_sell_mv(int n_brows, int R,
     if (threadIdx.x != 0) return;
     bool ok = true;
     int issued = min(NS, ns);
+    const uint64_t pol = l2_evict_first_policy();
     for (int s = NS; s < ns; ++s) {
       const int k = s % NS;
       if (!mbar_wait(empty + k, (uint32_t)((s / NS) - 1) & 1u)) {
@@ -157,7 +117,7 @@ __global__ void __launch_bounds__(kSellMaxThreads) k_sell_mv(int n_brows, int R,
         break;
       }
       mbar_expect_tx(full + k, chunk);
-      bulk_g2s(stage + (size_t)k * chunk_elems, src + (int64_t)s * chunk_elems, chunk, full + k);
+      bulk_g2s_policy(stage + (size_t)k * chunk_elems, src + (int64_t)s * chunk_elems, chunk, full + k, pol);
       issued = s + 1;
     }
     for (int s = max(issued - NS, 0); s < issued; ++s)  // own copies still in flight
@@ -412,12 +372,13 @@ static int sell_choose_rows(const Bsr& M, int kind, int sm_count) {
   return best_r;
 }
 
-static void sell_build_kind(Sell& S, const Bsr& M, int kind, cudaStream_t st, int sm_count) {
+// Sliced layout of M with value kind `kind`; group size R_fixed, or (0) chosen for the product kernel.
+static void sell_build_kind(Sell& S, const Bsr& M, int kind, cudaStream_t st, int sm_count, int R_fixed = 0) {
   sell_free(S);
   const int d = M.d;
   if (!(d == 3 || d == 6 || d == 10 || d == 15 || d == 21)) return;
   const int n = M.n_brows;
-  const int R = sell_choose_rows(M, kind, sm_count);
+  const int R = R_fixed > 0 ? R_fixed : sell_choose_rows(M, kind, sm_count);
   const int ng = (n + R - 1) / R;
   std::vector<int> goff(ng + 1, 0);
   for (int g = 0; g < ng; ++g) {
@@ -484,6 +445,12 @@ void sell_build(Bsr& M, cudaStream_t st, int sm_count) {
     return;
   }
   sell_build_kind(M.sell, M, M.dt == PUM_BF16 ? kKindBF16 : kKindF32, st, sm_count);
+}
+
+void sell_build_rows(Sell& S, const Bsr& M, int R, cudaStream_t st) {
+  PUM_CHECK(M.dt == PUM_F32 || M.dt == PUM_BF16, PUM_ERR_UNSUPPORTED, "sliced layout: FP32 or BF16 values");
+  PUM_CHECK(R > 0, PUM_ERR_INVALID_ARG, "sliced layout: group size");
+  sell_build_kind(S, M, M.dt == PUM_BF16 ? kKindBF16 : kKindF32, st, 0, R);
 }
 
 void sell_build_df(Sell& S, const Bsr& M64, cudaStream_t st, int sm_count) {

@@ -50,8 +50,10 @@ static void fsai_apply_epi(pum_ctx* ctx, pum_hier* h, int l, const void* r, int 
   Level& L = h->lv[l];
   const int vdt = L.vdt;
   const bool fin = (l == 0);
+  const bool fused = L.gg.S.R > 0;  // G (or G1) read once: partial products, then the gather
   EpiArgs s{};
   if (!h->fp.nested) {
+    if (fused) return gg_apply(ctx, L.gg, r, epi, e, fin ? PUM_TK_G : -1, fin ? PUM_TK_GT : -1);
     s.y = L.t;
     bsr_mv(ctx, L.G, vdt, r, EPI_SET, s, fin ? PUM_TK_G : -1);
     bsr_mv(ctx, L.GT, vdt, L.t, epi, e, fin ? PUM_TK_GT : -1);
@@ -59,6 +61,11 @@ static void fsai_apply_epi(pum_ctx* ctx, pum_hier* h, int l, const void* r, int 
   }
   s.y = L.t;
   bsr_mv(ctx, L.F0, vdt, r, EPI_SET, s, fin ? PUM_TK_G : -1);
+  if (fused) {  // t <- G1^T G1 t (the gather runs after the partial products have read t)
+    gg_apply(ctx, L.gg, L.t, EPI_SET, s, fin ? PUM_TK_G : -1, fin ? PUM_TK_GT : -1);
+    bsr_mv(ctx, L.F0T, vdt, L.t, epi, e, fin ? PUM_TK_GT : -1);
+    return;
+  }
   s.y = L.u;
   bsr_mv(ctx, L.G1, vdt, L.t, EPI_SET, s, fin ? PUM_TK_G : -1);
   s.y = L.t;

@@ -408,7 +408,11 @@ def test_fp32_form_double_float_residuals(lib):
     for form in ("df", "fp64op"):
         assert out[form][0]["iters"] == out["f64"][0]["iters"]
         h, h64 = np.array(out[form][0]["history"]), np.array(out["f64"][0]["history"])
-        assert np.max(np.abs(h - h64) / h64) <= 1e-2  # FP32 smoothing perturbs each cycle slightly
+        # FP32 smoothing perturbs each cycle by FP32 rounding; the recursive residual history of
+        # flexible PCG then drifts from the FP64 form's, most at the last iterations (measured
+        # up to 6.5e-3 with FP64 products, 8.0e-3 with the two-product FSAI application, 1.1e-2
+        # with the fused one, whose FP32 sums run in another order)
+        assert np.max(np.abs(h - h64) / h64) <= 2e-2
         assert norm_rel(out[form][1], out["f64"][1]) <= 1e-7
 
 
@@ -537,6 +541,59 @@ def test_sliced_layout_products_on_large_levels(lib, d, side):
     ref = fsai.fsai(A, fsai.diag_pattern(A.n_rows))  # block Jacobi (Remark 2.4): cheap at this size
     xr = cheb.cheb4(A.matvec, lambda r: fsai.apply_M(ref.G, r), b, None, outs[True][1], 3)
     assert norm_rel(outs[True][0], xr) <= 1e-5
+
+
+def _round_to(blocks, g):
+    import torch
+    dt = torch.float32 if g == "f32" else torch.bfloat16
+    return torch.from_numpy(blocks).to(dt).to(torch.float64).numpy()
+
+
+@pytest.mark.parametrize("d,side,g,nested", [(10, 66, "f32", False), (6, 90, "f32", False), (21, 65, "bf16", False),
+                                             (15, 66, "f32", False), (10, 66, "f32", True)])
+def test_fused_fsai_application_matches_two_products(lib, d, side, g, nested):
+    """On sliced levels z = G^T (G r) reads G once (partial products G_ji^T t_j, then a fixed-order
+    gather; for nested FSAI the inner G1^T G1).  Adaptive rows of uneven length give padding
+    slots, groups with fewer slots than the longest one (the persistent kernel reuses its
+    buffers across such groups) and the side a ragged last group.  z must equal the FP64 product of the exported
+    factors rounded to their storage precision (FP32 accumulation), match the two-product form,
+    repeat bit for bit, and Chebyshev smoothing through it must match the two-product form."""
+    import os
+    A = _random_block_spd(side, d, seed=40 + d)
+    P = bk.from_blocks(A.n_rows, 1, d, {(i, 0): np.eye(d) for i in range(A.n_rows)})
+    N = A.n_rows * d
+    r = pin.normal_vector(N, 12)
+    b = pin.normal_vector(N, 13)
+    outs = {}
+    for fused in (True, False):
+        if not fused:
+            os.environ["PUM_NO_FUSED_FSAI"] = "1"
+        try:
+            c = lib.Context(0)
+        finally:
+            os.environ.pop("PUM_NO_FUSED_FSAI", None)
+        H = lib.Hierarchy.from_bsr(c, [to_view(A), None], [to_pview(P)])
+        H.setup(p0="lower", adaptive=True, t_max=3, nested=nested, k=3, smooth="f32", g=g, mixed_levels=0)
+        z, z2, x = cuda(np.zeros(N)), cuda(np.zeros(N)), cuda(np.zeros(N))
+        H.fsai_apply(0, cuda(r), z)
+        H.fsai_apply(0, cuda(r), z2)
+        H.cheb4_smooth(0, cuda(b), x, True)
+        c.sync()  # raises on a device status (a bounded wait that expired)
+        mats = [from_export(H.export(0, w)) for w in ((lib.PUM_MAT_F0, lib.PUM_MAT_G1) if nested else (lib.PUM_MAT_G,))]
+        outs[fused] = (host(z), host(z2), host(x), mats)
+        H.close()
+        c.close()
+    zf, zf2, xf, mats = outs[True]
+    assert np.array_equal(zf, zf2)
+    assert norm_rel(zf, outs[False][0]) <= 1e-5
+    assert norm_rel(xf, outs[False][2]) <= 1e-5
+    rounded = [bk.BlockCSR(M.n_rows, M.n_cols, M.d, M.indptr, M.indices, _round_to(M.blocks, g)) for M in mats]
+    v = r.astype(np.float32).astype(np.float64)
+    for M in rounded:
+        v = M.matvec(v)
+    for M in reversed(rounded):
+        v = M.transpose().matvec(v)
+    assert norm_rel(zf, v) <= 1e-5
 
 
 def test_invalid_arguments_are_reported(lib, ctx, static_pair):
