@@ -193,13 +193,13 @@ __global__ void __launch_bounds__(kGgMaxThreads) k_gg_partial(int n_groups, int 
   const int p = t / RDp, tl = t - p * RDp;
   const bool computes = tl < RD;
   const int j = computes ? tl / D : 0;
+  const int bpt = nct / D, c3 = t % D;  // step 3: blocks per pass, this thread's component
   int k = 0;
   for (int g = blockIdx.x; g < n_groups; g += gridDim.x, ++k) {
     const int b = k & 1;
     const uint32_t ph = (uint32_t)(k >> 1) & 1u;
     const MT* stg = stage(b);
     float* xs = xsb(b);
-    const int* scol = scolb(b);
     const int* spos = sposb(b);
     float acc0 = 0.f, acc1 = 0.f;
     int ns = 0;
@@ -222,7 +222,8 @@ __global__ void __launch_bounds__(kGgMaxThreads) k_gg_partial(int n_groups, int 
         }
         if (computes) {
           const MT* a = stg + (size_t)s * chunk_elems + tl;
-          const float* xr = xs + (s * R + j) * D;
+          float xr[D];
+          load_smem_row<D, float>(xs + (s * R + j) * D, xr);
 #pragma unroll
           for (int cc = 0; cc < D; ++cc) {
             if (cc & 1)
@@ -250,8 +251,7 @@ __global__ void __launch_bounds__(kGgMaxThreads) k_gg_partial(int n_groups, int 
       float tv[D];
 #pragma unroll
       for (int q = 0; q < D; ++q) tv[q] = ts[jj * D + q];
-      for (int s = p; s < ns; s += P) {
-        if (scol[s * R + jj] < 0) continue;  // padding slot of a shorter row, or a row past the end
+      for (int s = p; s < ns; s += P) {  // padding blocks are zero; step 3 does not store them
         float a[D];
         load_smem_row<D, MT>(stg + (size_t)s * chunk_elems + c * RD + jj * D, a);
         float v0 = 0.f, v1 = 0.f;
@@ -268,11 +268,12 @@ __global__ void __launch_bounds__(kGgMaxThreads) k_gg_partial(int n_groups, int 
     named_barrier(1, nct);
 
     // 3. each block's d partial products, contiguous, at its position in G^T's block order
-    for (int i = t; i < ns * RD; i += nct) {
-      const int sj = i / D;
-      const int pos = spos[sj];
-      if (pos >= 0) w[(int64_t)pos * D + (i - sj * D)] = xs[i];
-    }
+    //    (thread of component c3 of every bpt-th block)
+    if (t < bpt * D)
+      for (int sj = t / D; sj < ns * R; sj += bpt) {
+        const int pos = spos[sj];
+        if (pos >= 0) w[(int64_t)pos * D + c3] = xs[sj * D + c3];
+      }
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(empty + b);  // this warp is done with buffer b
   }
@@ -294,16 +295,14 @@ __global__ void __launch_bounds__(256) k_gg_gather(int n_brows, const int* __res
   pdl_wait();  // w, and the epilogue's vectors, come from the preceding kernels
   const float* wc = w + c;
   float acc = 0.f;
-  int q = q0;
-  for (; q + 4 <= q1; q += 4) {  // four independent loads in flight, summed in block order
-    const float v0 = wc[(int64_t)q * D], v1 = wc[(int64_t)(q + 1) * D];
-    const float v2 = wc[(int64_t)(q + 2) * D], v3 = wc[(int64_t)(q + 3) * D];
-    acc += v0;
-    acc += v1;
-    acc += v2;
-    acc += v3;
+  for (int q = q0; q < q1; q += 8) {  // eight independent loads in flight, summed in block order
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = q + u < q1 ? wc[(int64_t)(q + u) * D] : 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (q + u < q1) acc += v[u];
   }
-  for (; q < q1; ++q) acc += wc[(int64_t)q * D];
   pdl_release();
   if (live) epilogue<EPI, float, float, YT, X2T>(e, u, acc);
 }
