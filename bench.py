@@ -95,6 +95,16 @@ def profiled_traffic(profile, sources):
         return None
 
 
+def max_over_ranks(value: float, device: str) -> float:
+    """The largest value over the ranks of the default process group (the job's time is its
+    slowest replica's)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -419,9 +429,7 @@ def main():
     launches = ctx.launches - launches0
     kt_live = ctx.timing_read()
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(total_ms, "cuda")
     ms_per_solve = total_ms / args.steps
     iters = reps[-1]["iters"]
     # per-class breakdown from an instrumented repeat of the same solves
@@ -495,6 +503,7 @@ def main():
                      "largest_total_class": dom},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},
+        "job_solves_per_s": world * args.steps / (total_ms * 1e-3),  # all replicas' solves / slowest rank's time
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "variants": variants,

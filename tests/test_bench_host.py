@@ -1,0 +1,58 @@
+"""Host logic of bench.py without a GPU: the max-over-ranks reduction of the replicas' times on
+two gloo ranks, the reference arm's rank handling, and the algorithmic byte model of the
+roofline kernels on the benchmark's finest level."""
+import os
+import socket
+
+import pytest
+
+import bench
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        q.put((rank, bench.max_over_ranks(1.5 + rank, "cpu")))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_on_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert got == {0: 2.5, 1: 2.5}
+
+
+def test_reference_arm_runs_on_rank_zero_only(capsys, monkeypatch):
+    import argparse
+    monkeypatch.setenv("RANK", "1")
+    args = argparse.Namespace(steps=1, warmup=0, gpus=2, impl="reference")
+    assert bench.run_reference(args) is None
+    assert capsys.readouterr().out == ""
+
+
+@pytest.mark.parametrize("fused,kernel,expected", [(True, "g", 322_006_180), (False, "gt", 314_204_300)])
+def test_roofline_bytes_of_the_finest_level(fused, kernel, expected):
+    """nnzb(G) = 719,335 blocks of 10 x 10 (adaptive FSAI, t_max = 6), N = 655,360: G's values and
+    columns once, plus r and the partial products (fused) or t, p, e and the FP64 iterate."""
+    info = {"d": 10, "n": 65536, "nnzb_G": 719_335, "nnzb_A": 586_756, "fused_fsai": int(fused)}
+    ab = bench.algorithmic_bytes(info, 4, 4, 4, 8)
+    assert ab[kernel] == expected
+    assert bench.ROOFLINE[fused][0] == kernel
