@@ -42,6 +42,7 @@ namespace {
 constexpr int kGgMaxThreads = 1024;
 constexpr int kGgBuffers = 2;
 constexpr int kGgMaxParts = 4;  // consumer partitions of a group's slots
+constexpr int kGgPre = 4;       // slot entries per producer lane held in registers (32 x 4 per group)
 
 // Shared memory: barriers (full per buffer and slot, meta and empty per buffer), then per buffer
 // the group's slots, its r segments (reused for the staged partial products), its block columns
@@ -123,11 +124,21 @@ __global__ void __launch_bounds__(kGgMaxThreads) k_gg_partial(int n_groups, int 
     for (int g = blockIdx.x; g < n_groups; g += gridDim.x, ++k) {
       const int b = k & 1;
       const uint32_t ph = (uint32_t)(k >> 1) & 1u;
+      // The group's extent, block columns and G^T positions (constant data) are loaded into
+      // registers first, so that their latency overlaps the wait for the buffer.
+      const int s0 = __ldg(goff + g), ns = __ldg(goff + g + 1) - s0;
+      const int m = ns * R;
+      int pc[kGgPre], pp[kGgPre];
+#pragma unroll
+      for (int u = 0; u < kGgPre; ++u) {
+        const int i = lane + 32 * u;
+        pc[u] = i < m ? __ldg(cols + (int64_t)s0 * R + i) : 0;
+        pp[u] = i < m ? __ldg(tpos + (int64_t)s0 * R + i) : -1;
+      }
       if (k >= kGgBuffers && !__all_sync(0xffffffffu, mbar_wait(empty + b, ph ^ 1u))) {  // use k - 2 released
         ok = false;
         break;
       }
-      const int s0 = __ldg(goff + g), ns = __ldg(goff + g + 1) - s0;
       if (lane == 0) {
         ginfo[b][0] = s0;
         ginfo[b][1] = ns;
@@ -142,10 +153,17 @@ __global__ void __launch_bounds__(kGgMaxThreads) k_gg_partial(int n_groups, int 
         // a buffer completes once per use and its parity stays that of the use
         for (int s = ns; s < ns_max; ++s) mbar_arrive(full + b * ns_max + s);
       }
-      // block columns and G^T positions of the group (one load latency for the warp) ...
       int* scol = scolb(b);
       int* spos = sposb(b);
-      for (int i = lane; i < ns * R; i += 32) {
+#pragma unroll
+      for (int u = 0; u < kGgPre; ++u) {
+        const int i = lane + 32 * u;
+        if (i < m) {
+          scol[i] = pc[u];
+          spos[i] = pp[u];
+        }
+      }
+      for (int i = lane + 32 * kGgPre; i < m; i += 32) {  // entries beyond the registers' share
         cp_async4(scol + i, cols + (int64_t)s0 * R + i);
         cp_async4(spos + i, tpos + (int64_t)s0 * R + i);
       }
@@ -156,11 +174,11 @@ __global__ void __launch_bounds__(kGgMaxThreads) k_gg_partial(int n_groups, int 
         waited = true;
       }
       mbar_arrive(meta + b);  // releases the columns and positions
-      // ... then the r segment of every slot (column 0 for padding, against zero values), landing
-      // on the meta barrier without holding registers
+      // the r segment of every slot (column 0 for padding, against zero values), landing on the
+      // meta barrier without holding registers
       float* xs = xsb(b);
-      for (int sj = lane; sj < ns * R; sj += 32) {
-        const float* src = x + (int64_t)max(scol[sj], 0) * D;
+      auto gather = [&](int sj, int col) {
+        const float* src = x + (int64_t)max(col, 0) * D;
         float* dst = xs + sj * D;
         if constexpr ((D % 2) == 0) {
 #pragma unroll
@@ -169,7 +187,11 @@ __global__ void __launch_bounds__(kGgMaxThreads) k_gg_partial(int n_groups, int 
 #pragma unroll
           for (int c = 0; c < D; ++c) cp_async4(dst + c, src + c);
         }
-      }
+      };
+#pragma unroll
+      for (int u = 0; u < kGgPre; ++u)
+        if (lane + 32 * u < m) gather(lane + 32 * u, pc[u]);
+      for (int sj = lane + 32 * kGgPre; sj < m; sj += 32) gather(sj, scol[sj]);
       cp_async_mbar_arrive_noinc(meta + b);
     }
     // own copies still in flight (normally all consumed already)
