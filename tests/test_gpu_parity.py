@@ -683,7 +683,7 @@ def test_kernel_timing_counts_every_finest_launch(lib, small_biharmonic, graph):
     assert kt_gt["gt"][0] == kt["gt"][0] and all(kt_gt[n][0] == 0 for n in ("resid", "g", "pcg_ap", "resid64"))
 
 
-# --------------------------------------------- batched independent problems
+# --------------------------------------------------------------- batched independent problems
 
 def test_batch_setup_and_solves_match_single_calls(lib):
     """Uneven instances (sides 8, 12 (3x3 coarsest), 16; degrees 2 and 3), three right-hand sides
