@@ -178,7 +178,12 @@ def solve_batch(workers, items, rtol: float = 1e-8, maxit: int = 200, flexible: 
 
 
 class Hierarchy:
-    """Level hierarchy {A_l, P_l, G_l, beta_l} owned by the library (pum_hier)."""
+    """Level hierarchy {A_l, P_l, G_l, beta_l} owned by the library (pum_hier).
+
+    setup, pcg, bicgstab and convergence_factor return once the work is done and raise on a
+    device-side status; cheb4_smooth, vcycle and the single steps only queue their kernels on
+    the context's stream: Context.sync() waits for them and raises on a device-side status (a
+    bounded wait that expired)."""
 
     def __init__(self, ctx: Context, handle: C.c_void_p):
         self.ctx, self.h, self.lib = ctx, handle, ctx.lib
