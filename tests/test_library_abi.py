@@ -64,3 +64,42 @@ def test_missing_device_is_an_error_not_a_fallback(lib):
     from paper_2509_06744_gb300 import Context, PumError
     with pytest.raises(PumError):
         Context(0)
+
+
+# C struct of include/pum.h -> ctypes mirror in the binding
+_STRUCTS = {"pum_bsr_view": "BsrView", "pum_bsr_host": "BsrHost", "pum_problem": "Problem",
+            "bfsai_params": "FsaiParams", "smoother_params": "SmootherParams", "pcg_report": "PcgReport",
+            "pum_level_info": "LevelInfo"}
+
+
+def _c_layout(tmp_path):
+    """sizeof and field offsets of the header's structs, from a C program compiled with gcc."""
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not available")
+    from paper_2509_06744_gb300 import _lib
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "pum.h"', "int main(void) {"]
+    for cname, pyname in _STRUCTS.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in getattr(_lib, pyname)._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return {(a, b): int(c) for a, b, c in (line.split() for line in out.splitlines())}
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every ctypes mirror has the C struct's field names, offsets and size (a field added on one
+    side only, or in another order, fails here)."""
+    from paper_2509_06744_gb300 import _lib
+    c = _c_layout(tmp_path)
+    for cname, pyname in _STRUCTS.items():
+        py = getattr(_lib, pyname)
+        assert C.sizeof(py) == c[(cname, "size")], cname
+        for f, _ in py._fields_:
+            assert getattr(py, f).offset == c[(cname, f)], f"{cname}.{f}"
