@@ -103,3 +103,32 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert C.sizeof(py) == c[(cname, "size")], cname
         for f, _ in py._fields_:
             assert getattr(py, f).offset == c[(cname, f)], f"{cname}.{f}"
+
+
+def test_c_example_builds_against_the_library(tmp_path):
+    """tests/c_example/solve_biharmonic.c uses only include/pum.h (and the CUDA runtime for its
+    vectors): it compiles warning-free, links against libpum.so and, without a CUDA device, reports
+    the failed pum_create (exit status 2) instead of crashing; with one it solves (exit status 0)."""
+    import shutil
+    import subprocess
+    from paper_2509_06744_gb300 import _lib
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    if not shutil.which("gcc") or not os.path.exists(os.path.join(cuda, "include", "cuda_runtime.h")):
+        pytest.skip("gcc or the CUDA headers are not available")
+    _lib.load()  # builds the library when it is missing
+    libdir = os.path.dirname(_lib.lib_path())
+    exe = tmp_path / "solve_biharmonic"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        "-I", os.path.join(cuda, "include"), os.path.join(ROOT, "tests", "c_example", "solve_biharmonic.c"),
+                        "-L", libdir, "-lpum", "-L", os.path.join(cuda, "lib64"), "-lcudart",
+                        f"-Wl,-rpath,{libdir}", f"-Wl,-rpath,{os.path.join(cuda, 'lib64')}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    import torch
+    if torch.cuda.is_available():
+        assert run.returncode == 0, run.stderr
+        assert "converged" in run.stdout
+    else:
+        assert run.returncode == 2, run.stderr
+        assert "pum_create" in run.stderr
