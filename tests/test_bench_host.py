@@ -56,3 +56,22 @@ def test_roofline_bytes_of_the_finest_level(fused, kernel, expected):
     ab = bench.algorithmic_bytes(info, 4, 4, 4, 8)
     assert ab[kernel] == expected
     assert bench.ROOFLINE[fused][0] == kernel
+
+
+def test_reference_arm_prints_the_contract_line(capsys, monkeypatch):
+    """The reference arm (the oracle on the host cores) prints one JSON line with the metric,
+    a cpu_baseline describing the sample and an e2e entry without host-device copies."""
+    import argparse
+    import json
+    monkeypatch.delenv("RANK", raising=False)
+    real = bench.oracle_sample
+    monkeypatch.setattr(bench, "oracle_sample", lambda seconds_budget=0.0: real(seconds_budget=0.0))
+    bench.run_reference(argparse.Namespace(steps=1, warmup=0, gpus=1, impl="reference"))
+    lines = [line for line in capsys.readouterr().out.splitlines() if line.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] > 0 and d["higher_is_better"] is False
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
