@@ -82,13 +82,17 @@ def from_blocks(n_rows: int, n_cols: int, d: int, entries: dict) -> BlockCSR:
 
 
 def from_pattern_and_scalar(pattern: list[list[int]], n_cols: int, d: int, S) -> BlockCSR:
-    """Blocks of the scalar matrix S (scipy or dense) on a given block pattern."""
-    S = sp.csr_matrix(S)
+    """Blocks of the scalar matrix S (scipy or dense) on a given block pattern (blocks of the
+    pattern that S does not store are zero)."""
+    B = sp.csr_matrix(S).tobsr(blocksize=(d, d))
+    B.sort_indices()
     entries = {}
     for i, cols in enumerate(pattern):
-        rows = S[i * d:(i + 1) * d].toarray()
+        lo, hi = int(B.indptr[i]), int(B.indptr[i + 1])
+        where = dict(zip(B.indices[lo:hi].tolist(), range(lo, hi)))
         for j in cols:
-            entries[(i, j)] = rows[:, j * d:(j + 1) * d]
+            q = where.get(j)
+            entries[(i, j)] = B.data[q] if q is not None else np.zeros((d, d))
     return from_blocks(len(pattern), n_cols, d, entries)
 
 

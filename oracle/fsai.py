@@ -14,6 +14,13 @@ Test infrastructure only (never imported by the CUDA library).
 * ``nested_fsai``: Section 2.2 with one level of nesting:
   A_1 = F_0 A F_0^T, F_1 the (adaptive) FSAI of A_1 with the same parameters,
   S^ = diag_B(F_1 A_1 F_1^T), M = F^^T S^^{-1} F^ with F^ = F_1 F_0.
+  The FSAI of A_1 needs A_1 to be SPD, which the paper takes for granted.  In FP64
+  the computed A_1 can lose definiteness (a diagonal block whose Schur-complement
+  value is far below the rounding of the triple product).  When any local matrix of
+  the inner FSAI (A_1[P~_k, P~_k] or S_kk) fails its Cholesky factorisation, the
+  inner level falls back to block Jacobi (the diagonal pattern, Remark 2.4), whose
+  blocks diag_B(A_1) = S of the outer FSAI by Lemma 2.3; M is then the plain
+  (non-nested) block-FSAI G^T G.
 """
 from __future__ import annotations
 
@@ -58,19 +65,38 @@ class FSAI:
         return float(sum(np.linalg.slogdet(s)[1] for s in self.S))
 
 
+class NotSPD(np.linalg.LinAlgError):
+    """A local matrix of Definition 2.2 (A[P~_k, P~_k] or S_kk) is not numerically SPD in FP64."""
+
+    def __init__(self, k: int, what: str):
+        super().__init__(f"{what} of block row {k} is not numerically SPD")
+        self.row = k
+
+
+def _require_spd(X: np.ndarray, k: int, what: str) -> None:
+    """Definition 2.2 assumes SPD local matrices; in FP64 that is decided by their Cholesky."""
+    if not _is_spd(X):
+        raise NotSPD(k, what)
+
+
 def fsai_row(A: bk.BlockCSR, k: int, Pk: list[int]):
-    """F row k (dict col -> block), S_kk, per Definition 2.2."""
+    """F row k (dict col -> block), S_kk, per Definition 2.2.
+
+    Raises NotSPD when A[P~_k, P~_k] or S_kk fails its Cholesky factorisation."""
     d = A.d
     Pt = [j for j in Pk if j != k]
     row = {k: np.eye(d)}
     Akk = A.block(k, k)
     if not Pt:
+        _require_spd(Akk, k, "S_kk")
         return row, Akk.copy()
     App = dense(A, Pt, Pt)
+    _require_spd(App, k, "A[P~_k, P~_k]")
     Akp = dense(A, [k], Pt)
     Apk = dense(A, Pt, [k])
     Fk = -np.linalg.solve(App.T, Akp.T).T          # -A[k,P~] A[P~,P~]^{-1}
     S = Akk - Akp @ np.linalg.solve(App, Apk)
+    _require_spd(S, k, "S_kk")
     for b, j in enumerate(Pt):
         row[j] = Fk[:, b * d:(b + 1) * d]
     return row, S
@@ -226,6 +252,11 @@ class NestedFSAI:
     A1: bk.BlockCSR
     inner: FSAI            # FSAI of A1: its G is G_1 = S^^{-1/2} F_1
     outer_pattern: list
+    inner_nested: bool = True   # False: A1 was not numerically SPD and the inner level is block Jacobi
+
+    def logdet_S(self) -> float:
+        """sum_k log det S_kk of the inner FSAI (the outer S under the block-Jacobi fallback)."""
+        return self.inner.logdet_S()
 
     def apply(self, r: np.ndarray) -> np.ndarray:
         """z = F0^T G1^T G1 F0 r."""
@@ -241,8 +272,22 @@ def nested_fsai(A: bk.BlockCSR, P0: list[list[int]], t_max: int, tau: float = 1.
     outer = adaptive_fsai(A, P0, t_max, tau, tie_rel).fsai if adaptive else fsai(A, P0)
     F0 = outer.F
     A1 = bk.galerkin_product(F0, A, F0.transpose())
-    inner = adaptive_fsai(A1, P0, t_max, tau, tie_rel).fsai if adaptive else fsai(A1, P0)
+    try:
+        inner = adaptive_fsai(A1, P0, t_max, tau, tie_rel).fsai if adaptive else fsai(A1, P0)
+    except NotSPD:
+        return NestedFSAI(F0, A1, block_jacobi_from_schur(outer), outer.pattern, inner_nested=False)
     return NestedFSAI(F0, A1, inner, outer.pattern)
+
+
+def block_jacobi_from_schur(outer: FSAI) -> FSAI:
+    """Inner block Jacobi of A_1 = F_0 A F_0^T (Remark 2.4: F = I, S = diag_B(A_1)), with
+    diag_B(A_1) taken as the outer Schur complements S (equal by Lemma 2.3) and its G blocks
+    L_S^{-1}; then F_0^T G_1^T G_1 F_0 = G^T G of the outer FSAI."""
+    n, d = outer.S.shape[0], outer.S.shape[1]
+    ent = {(k, k): sla.solve_triangular(np.linalg.cholesky(outer.S[k]), np.eye(d), lower=True)
+           for k in range(n)}
+    eye = {(k, k): np.eye(d) for k in range(n)}
+    return FSAI(diag_pattern(n), bk.from_blocks(n, n, d, eye), outer.S.copy(), bk.from_blocks(n, n, d, ent))
 
 
 def apply_M(G: bk.BlockCSR, r: np.ndarray) -> np.ndarray:

@@ -231,3 +231,116 @@ def test_nested_with_diagonal_inner_pattern_equals_plain(small_biharmonic):
     nested = Gh.T @ (Gh @ r)
     plain = fsai.apply_M(outer.G, r)
     assert np.max(np.abs(nested - plain)) <= 1e-11 * np.max(np.abs(plain))
+
+
+def _rows_only(A: bk.BlockCSR, rows) -> bk.BlockCSR:
+    """A with only the given block rows stored (the others empty): a window of A."""
+    keep = set(rows)
+    ent = {(i, int(j)): A.blocks[p] for i in keep for p, j in
+           zip(range(A.indptr[i], A.indptr[i + 1]), A.row(i))}
+    return bk.from_blocks(A.n_rows, A.n_cols, A.d, ent)
+
+
+def _grid_window(k, m, radius):
+    kx, ky = k % m, k // m
+    return [iy * m + ix for iy in range(max(ky - radius, 0), min(ky + radius + 1, m))
+            for ix in range(max(kx - radius, 0), min(kx + radius + 1, m))]
+
+
+@pytest.mark.parametrize("p0", ["lower", "diag"])
+def test_adaptive_row_equals_adaptive_fsai_on_every_row(small_biharmonic, p0):
+    """Algorithm 1 row by row: a row's scores depend on A and its own pattern only, so running
+    the steps for one row alone (adaptive_row, used at sizes where the whole matrix is out of
+    reach) gives that row of the whole-matrix run; also from a window of A of radius 8 around the
+    row (t_max = 6 grows a pattern by at most 6 grid steps, candidates one further)."""
+    A = small_biharmonic.A[0]            # 16 x 16 patches, d = 10
+    m = 16
+    P0 = fsai.lower_pattern(A) if p0 == "lower" else fsai.diag_pattern(A.n_rows)
+    whole = fsai.adaptive_fsai(A, P0, 6).fsai.pattern
+    grown = 0
+    for k in range(A.n_rows):
+        row = fsai.adaptive_row(A, k, P0[k], 6)
+        assert row == whole[k], f"row {k}"
+        grown += len(row) - len(P0[k])
+    assert grown >= 3 * A.n_rows          # the rows really grew
+    for k in (0, 17, 8 * 16 + 8, 255, 100):
+        Aw = _rows_only(A, _grid_window(k, m, 8))
+        assert fsai.adaptive_row(Aw, k, P0[k], 6) == whole[k], f"windowed row {k}"
+
+
+def _inadmissible_candidate_matrix():
+    """A = X^T X with X = [[I, I, B], [0, 0, E]] (blocks of 2): block columns 0 and 1 of A are
+    equal, so once block 0 is in a row's pattern, block 1 has W_1 = A_11 - A_10 A_00^-1 A_01 = 0
+    (exactly: A_00 = A_01 = A_11 = I and B, E hold small integers)."""
+    I2 = np.eye(2)
+    B = np.array([[1.0, 2.0], [0.0, 1.0]])
+    E = np.array([[2.0, 1.0], [1.0, 3.0]])
+    X = np.block([[I2, I2, B], [np.zeros((2, 2)), np.zeros((2, 2)), E]])
+    return _block_csr_from_dense(X.T @ X, 2)
+
+
+def test_candidate_without_computable_gain_is_inadmissible():
+    """Algorithm 1 assumes SPD A, so every candidate's Schur complement W_c - H^T S^-1 H is SPD.
+    In FP64 a candidate whose complement fails its Cholesky factorisation has no rho_c: it is
+    skipped, and a row left with no computable candidate retires (it is not grown into a
+    singular local system)."""
+    Ab = _inadmissible_candidate_matrix()
+    r0 = fsai.row_rhos(Ab, 2, [2], [0, 1])
+    assert set(r0) == {0, 1} and r0[0] == r0[1] < 1.0          # tie: the smaller column is taken
+    assert fsai.choose(r0, 1e-9) == 0
+    assert fsai.row_rhos(Ab, 2, [0, 2], [1]) == {}              # W_1 = 0: not computable
+    res = fsai.adaptive_fsai(Ab, fsai.diag_pattern(3), 3)
+    assert res.fsai.pattern[2] == [0, 2]
+    assert fsai.adaptive_row(Ab, 2, [2], 3) == [0, 2]
+    # the retained pattern gives a valid FSAI: diag_B(G A G^T) = I on row 2
+    G, A = res.fsai.G.to_dense(), Ab.to_dense()
+    assert np.max(np.abs((G @ A @ G.T)[4:6, 4:6] - np.eye(2))) <= 1e-12
+
+
+def _indefinite_a1_matrix():
+    """A = X^T X (9 x 9, blocks of 3) with strongly coupled blocks: the adaptive outer FSAI
+    (from the diagonal, t_max = 2) succeeds, but the diagonal blocks of the computed
+    A_1 = F_0 A F_0^T have lost definiteness to the rounding of the triple product, far beyond
+    rounding noise (seeded; the margin is asserted by the test)."""
+    rng = np.random.default_rng(165)
+    N = 9
+    X = np.eye(N) + 1e4 * rng.standard_normal((N, N)) * (rng.random((N, N)) < 0.3)
+    X += np.diag(10.0 ** rng.uniform(-6, 0, N))
+    A = X.T @ X
+    return _block_csr_from_dense(0.5 * (A + A.T), 3)
+
+
+def test_nested_fsai_falls_back_to_block_jacobi_when_A1_is_not_spd():
+    """Section 2.2 on an A whose computed A_1 = F_0 A F_0^T is not numerically SPD: the inner
+    FSAI cannot be formed, and the inner level is block Jacobi of A_1 (Remark 2.4) with
+    diag_B(A_1) = S of the outer FSAI (Lemma 2.3), so M is the plain block-FSAI G^T G."""
+    Ab = _indefinite_a1_matrix()
+    P0 = fsai.diag_pattern(Ab.n_rows)
+    outer = fsai.adaptive_fsai(Ab, P0, 2).fsai
+    A1 = bk.galerkin_product(outer.F, Ab, outer.F.transpose())
+    worst = min(np.linalg.eigvalsh(0.5 * (A1.block(k, k) + A1.block(k, k).T))[0] / np.linalg.norm(A1.block(k, k))
+                for k in range(Ab.n_rows))
+    assert worst < -1e-10                          # indefinite well beyond rounding noise
+    with pytest.raises(fsai.NotSPD):
+        fsai.adaptive_fsai(A1, P0, 2)
+    nf = fsai.nested_fsai(Ab, P0, 2)
+    assert not nf.inner_nested
+    assert nf.inner.pattern == P0
+    assert nf.logdet_S() == pytest.approx(outer.logdet_S(), rel=1e-14)
+    r = np.random.default_rng(2).standard_normal(Ab.n_rows * Ab.d)
+    plain = fsai.apply_M(outer.G, r)
+    assert np.max(np.abs(nf.apply(r) - plain)) <= 1e-12 * np.max(np.abs(plain))
+
+
+def test_block_jacobi_from_schur_is_block_jacobi_of_A1(small_biharmonic):
+    """The fallback's blocks L_S^-1 equal block Jacobi of A_1 (Lemma 2.3: diag_B(F_0 A F_0^T) =
+    S) on a matrix where A_1 is well conditioned."""
+    A = small_biharmonic.A[2]
+    outer = fsai.fsai(A, fsai.lower_pattern(A))
+    A1 = bk.galerkin_product(outer.F, A, outer.F.transpose())
+    jac = fsai.fsai(A1, fsai.diag_pattern(A.n_rows))
+    fb = fsai.block_jacobi_from_schur(outer)
+    for k in range(A.n_rows):
+        ref = jac.G.block(k, k)
+        assert np.max(np.abs(fb.G.block(k, k) - ref)) <= 1e-10 * np.max(np.abs(ref))
+    assert fb.logdet_S() == pytest.approx(jac.logdet_S(), rel=1e-10)
