@@ -284,7 +284,12 @@ def test_anisotropic_solve_matches_oracle(lib, ctx):
     rep = H.pcg(b, x, rtol=1e-8, maxit=100)
     res = solver.solve(ref, h.b, rtol=1e-8)
     assert rep["converged"] and rep["iters"] == res.iters
-    assert np.max(np.abs(np.array(rep["history"]) - np.array(res.history))) <= 1e-10
+    # Example 5.2 is outside the benchmark workloads, whose FP64 histories meet 1e-12: its
+    # residual rises to 2.4 ||b|| at the first iteration, and the FSAI from the diagonal pattern
+    # of the anisotropic operator solves worse-conditioned local systems, so the bound is
+    # 1e-11 relative to max(1, ||r_j|| / ||b||) (measured 5.6e-12 at ||r_1|| / ||b|| = 2.4)
+    hg, ho = np.array(rep["history"]), np.array(res.history)
+    assert np.max(np.abs(hg - ho) / np.maximum(1.0, ho)) <= 1e-11
     H.close()
 
 
@@ -331,14 +336,14 @@ def test_convergence_factor_matches_oracle(variant_pairs, small_biharmonic, vari
 
 def test_bicgstab_with_v2k0_matches_oracle(variant_pairs, small_biharmonic):
     """BiCGStab preconditioned by the non-symmetric V(2k,0) cycle: same iterations, histories
-    within 1e-10, solution of the oracle's run."""
+    within 1e-12 (absolute, as for PCG), solution of the oracle's run."""
     H, ref = variant_pairs[("cheb4", "v2k0")]
     h = small_biharmonic
     x = cuda(np.zeros_like(h.b))
     rep = H.bicgstab(cuda(h.b), x, rtol=1e-8, maxit=100)
     res = solver.solve_bicgstab(ref, h.b, rtol=1e-8)
     assert rep["converged"] and rep["iters"] == res.iters
-    assert np.max(np.abs(np.array(rep["history"]) - np.array(res.history))) <= 1e-10
+    assert np.max(np.abs(np.array(rep["history"]) - np.array(res.history))) <= TOL_HISTORY
     assert norm_rel(host(x), res.x) <= 1e-8
 
 
@@ -402,17 +407,24 @@ def test_fp32_form_double_float_residuals(lib):
             H.setup(p0="lower", k=3, smooth="f32", g="f32")
         x = torch.zeros_like(b)
         rep = H.pcg(b, x, rtol=1e-8, maxit=100, flexible=form != "f64")
-        out[form] = (rep, host(x))
+        zb = torch.zeros_like(b)
+        H.vcycle(b, zb)
+        out[form] = (rep, host(x), host(zb))
         H.close()
         c.close()
+    h64 = np.array(out["f64"][0]["history"])
+    rho_min = float(np.min(h64[1:] / h64[:-1]))
     for form in ("df", "fp64op"):
         assert out[form][0]["iters"] == out["f64"][0]["iters"]
-        h, h64 = np.array(out[form][0]["history"]), np.array(out["f64"][0]["history"])
-        # FP32 smoothing perturbs each cycle by FP32 rounding; the recursive residual history of
-        # flexible PCG then drifts from the FP64 form's, most at the last iterations (measured
-        # up to 6.5e-3 with FP64 products, 8.0e-3 with the two-product FSAI application, 1.1e-2
-        # with the fused one, whose FP32 sums run in another order)
-        assert np.max(np.abs(h - h64) / h64) <= 2e-2
+        h = np.array(out[form][0]["history"])
+        # The FP32 cycle is the FP64 cycle perturbed by eta (relative, measured on b).  One
+        # flexible-PCG step moves the recursive residual by alpha A p, whose perturbation is
+        # about eta ||r_j||; relative to ||r_{j+1}|| = rho_j ||r_j|| that is eta / rho_j, and
+        # earlier perturbations are contracted by the later steps, so the histories agree to
+        # 2 eta / min_j rho_j relative.
+        eta = norm_rel(out[form][2], out["f64"][2])
+        assert eta <= 1e-3
+        assert np.max(np.abs(h - h64) / h64) <= 2.0 * eta / rho_min
         assert norm_rel(out[form][1], out["f64"][1]) <= 1e-7
 
 
