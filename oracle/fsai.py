@@ -10,7 +10,8 @@ Test infrastructure only (never imported by the CUDA library).
 * ``adaptive_fsai``: Algorithm 1 in the paper's order.  The admissible set is read
   structurally: c < k with c in the union of the A-patterns of the rows in P_k and
   c not in P_k; ties in the argmin of rho_c are broken by taking the smallest column
-  among those within a relative band tie_rel of the minimum.
+  among those within a relative band tie_rel of the minimum, and the stop test
+  rho_c* < tau takes the same band (rho_c* < tau (1 - tie_rel)).
 * ``nested_fsai``: Section 2.2 with one level of nesting:
   A_1 = F_0 A F_0^T, F_1 the (adaptive) FSAI of A_1 with the same parameters,
   S^ = diag_B(F_1 A_1 F_1^T), M = F^^T S^^{-1} F^ with F^ = F_1 F_0.
@@ -179,6 +180,13 @@ def choose(rhos: dict, tie_rel: float) -> int:
     return min(c for c, r in rhos.items() if r <= rmin * (1.0 + tie_rel))
 
 
+def accepts(rho_star: float, tau: float, tie_rel: float) -> bool:
+    """Algorithm 1's test rho_c* < tau, with the tie band: a gain below tie_rel relative to tau
+    is rounding (with tau = 1, a candidate whose coupling H_kc vanishes to rounding has
+    rho_c = 1 up to rounding), so it is not a gain."""
+    return rho_star < tau * (1.0 - tie_rel)
+
+
 @dataclasses.dataclass
 class AdaptiveResult:
     fsai: FSAI
@@ -205,7 +213,7 @@ def adaptive_fsai(A: bk.BlockCSR, P0: list[list[int]], t_max: int, tau: float = 
                 R.discard(k)
                 continue
             cstar = choose(rhos, tie_rel)
-            if rhos[cstar] < tau:
+            if accepts(rhos[cstar], tau, tie_rel):
                 P[k] = sorted(P[k] + [cstar])
             else:
                 R.discard(k)
@@ -232,7 +240,7 @@ def adaptive_row(A: bk.BlockCSR, k: int, P0k: list[int], t_max: int, tau: float 
         if not rhos:
             break
         cstar = choose(rhos, tie_rel)
-        if rhos[cstar] < tau:
+        if accepts(rhos[cstar], tau, tie_rel):
             Pk = sorted(Pk + [cstar])
         else:
             break

@@ -48,21 +48,38 @@ class Setup:
 
 
 def make_smoother(A: bk.BlockCSR, mode: str, P0: str, t_max: int, tau: float, nested: bool,
-                  tie_rel: float = 1e-9):
-    """Block-FSAI smoother of one level: returns (M callable, FSAI object(s))."""
+                  tie_rel: float = 1e-9, row_map=map):
+    """Block-FSAI smoother of one level: returns (M callable, FSAI object(s)).
+
+    row_map (a map over block rows, e.g. a process pool's) runs Algorithm 1 row by row with
+    adaptive_row: the rows of Algorithm 1 are independent, so this equals adaptive_fsai's
+    pattern (pinned by a test)."""
     p0 = fsai.lower_pattern(A) if P0 == "lower" else fsai.diag_pattern(A.n_rows)
     if nested:
         nf = fsai.nested_fsai(A, p0, t_max, tau, tie_rel, adaptive=(mode == "adaptive"))
         return nf.apply, nf
-    if mode == "adaptive":
+    if mode == "adaptive" and row_map is not map:
+        rows = list(row_map(_AdaptiveRow(A, p0, t_max, tau, tie_rel), range(A.n_rows)))
+        f = fsai.fsai(A, rows)
+    elif mode == "adaptive":
         f = fsai.adaptive_fsai(A, p0, t_max, tau, tie_rel).fsai
     else:
         f = fsai.fsai(A, p0)
     return (lambda r, G=f.G: fsai.apply_M(G, r)), f
 
 
+class _AdaptiveRow:
+    """Picklable per-row call of Algorithm 1 (fsai.adaptive_row) for a map over block rows."""
+
+    def __init__(self, A, P0, t_max, tau, tie_rel):
+        self.A, self.P0, self.t_max, self.tau, self.tie_rel = A, P0, t_max, tau, tie_rel
+
+    def __call__(self, k):
+        return fsai.adaptive_row(self.A, k, self.P0[k], self.t_max, self.tau, self.tie_rel)
+
+
 def build_setup(h: pum.Hierarchy, k: int, mode: str = "static", P0: str = "lower", t_max: int = 0,
-                tau: float = 1.0, nested: bool = False, lanczos_seed: int = 0) -> Setup:
+                tau: float = 1.0, nested: bool = False, lanczos_seed: int = 0, row_map=map) -> Setup:
     """FSAI smoothers, Lanczos beta = 1.01 lambda_max(M A) per level, coarse Cholesky."""
     levels = []
     L = len(h.A)
@@ -71,7 +88,7 @@ def build_setup(h: pum.Hierarchy, k: int, mode: str = "static", P0: str = "lower
         if l == L - 1:
             levels.append(Level(A, None, None, None, np.linalg.cholesky(A.to_dense())))
             continue
-        Mop, obj = make_smoother(A, mode, P0, t_max, tau, nested)
+        Mop, obj = make_smoother(A, mode, P0, t_max, tau, nested, row_map=row_map)
         Gop = _symmetric_form(obj, nested)
         lam = cheb.lanczos_lmax(lambda v: Gop(A, v), A.n_rows * A.d, seed=lanczos_seed + l)
         levels.append(Level(A, h.P[l], Mop, cheb.LANCZOS_SAFETY * lam, None))

@@ -344,3 +344,24 @@ def test_block_jacobi_from_schur_is_block_jacobi_of_A1(small_biharmonic):
         ref = jac.G.block(k, k)
         assert np.max(np.abs(fb.G.block(k, k) - ref)) <= 1e-10 * np.max(np.abs(ref))
     assert fb.logdet_S() == pytest.approx(jac.logdet_S(), rel=1e-10)
+
+
+def _weak_coupling_matrix(eps):
+    """Two blocks of 2: A = [[I, eps I], [eps I, I]]; candidate 0 of row 1 has H_10 = eps I, so
+    rho_0 = det(I - eps^2 I) = (1 - eps^2)^2 exactly in real arithmetic."""
+    I2 = np.eye(2)
+    return _block_csr_from_dense(np.block([[I2, eps * I2], [eps * I2, I2]]), 2)
+
+
+def test_stop_test_takes_the_tie_band():
+    """Algorithm 1 adds c* only when rho_c* < tau; with tau = 1 a candidate coupled to the row by
+    rounding alone has rho_c = 1 up to rounding, so the test takes the tie band: rho_c* must be
+    below tau (1 - tie_rel).  A gain of 2e-6 is taken, one of 2e-12 is not."""
+    strong = _weak_coupling_matrix(1e-3)
+    weak = _weak_coupling_matrix(1e-6)
+    assert fsai.row_rhos(strong, 1, [1], [0])[0] == pytest.approx((1 - 1e-6) ** 2, rel=1e-14)
+    assert 1.0 - fsai.row_rhos(weak, 1, [1], [0])[0] == pytest.approx(2e-12, rel=1e-3)
+    assert fsai.adaptive_fsai(strong, fsai.diag_pattern(2), 1).fsai.pattern[1] == [0, 1]
+    assert fsai.adaptive_fsai(weak, fsai.diag_pattern(2), 1).fsai.pattern[1] == [1]
+    assert fsai.adaptive_row(weak, 1, [1], 1) == [1]
+    assert fsai.accepts(1.0 - 2e-9, 1.0, 1e-9) and not fsai.accepts(1.0 - 5e-10, 1.0, 1e-9)
