@@ -20,7 +20,6 @@ Rank 0 prints one JSON line.  Under torchrun (N > 1) every rank solves its own r
 from __future__ import annotations
 
 import argparse
-import functools
 import json
 import os
 import statistics
@@ -166,67 +165,148 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-@functools.lru_cache(maxsize=1)
-def _oracle_setup():
-    """The oracle's hierarchy and smoother set-up for the 16x16-patch version of the workload."""
+# --------------------------------------------------------------------------- oracle baseline
+
+CPU_SAMPLE_M = 64  # patches per side of the oracle's sample of the workload
+
+
+def _oracle_assemble_strip(args):
+    from oracle import pum as opum
+    m, rows, pr = args
+    f = opum.fourier_source(pin.fourier_coefficients(pr.rhs_seed), pr.rhs_decay)
+    g = opum.nitsche_gamma(pr.equation, pr.p, m, pr.nitsche)
+    return _strip(opum.assemble(m, pr.p, pr.equation, g, f=f, with_mass=False, rows=rows), rows)
+
+
+def _oracle_prolong_strip(args):
+    from oracle import pum as opum
+    m_f, rows, p = args
+    return _strip(opum.prolongation(m_f, p, rows=rows), rows)
+
+
+def _strip(asm_or_mat, rows):
+    M = getattr(asm_or_mat, "A", asm_or_mat)
+    b = getattr(asm_or_mat, "b", None)
+    r0, r1 = rows[0], rows[-1] + 1
+    lo, hi = int(M.indptr[r0]), int(M.indptr[r1])
+    d = M.d
+    return (r0, r1, M.n_rows, M.n_cols, d, np.diff(M.indptr[r0:r1 + 1]), M.indices[lo:hi], M.blocks[lo:hi],
+            None if b is None else b[r0 * d:r1 * d])
+
+
+def _merge(parts):
+    from oracle import blocks as bk
+    parts = sorted(parts, key=lambda q: q[0])
+    n_rows, n_cols, d = parts[0][2], parts[0][3], parts[0][4]
+    indptr = np.zeros(n_rows + 1, dtype=np.int64)
+    np.cumsum(np.concatenate([q[5] for q in parts]), out=indptr[1:])
+    M = bk.BlockCSR(n_rows, n_cols, d, indptr, np.concatenate([q[6] for q in parts]),
+                    np.concatenate([q[7] for q in parts]))
+    b = None if parts[0][8] is None else np.concatenate([q[8] for q in parts])
+    return M, b
+
+
+def _strips(n, k):
+    edges = np.linspace(0, n, k + 1).astype(int)
+    return [list(range(edges[i], edges[i + 1])) for i in range(k) if edges[i + 1] > edges[i]]
+
+
+def _oracle_child(pr, m, n_levels, workers, solves, q):
+    """The oracle on the m x m version of the workload in a process of its own (BLAS threads 1):
+    the hierarchy (assembly and prolongations over row strips, Galerkin products) and the smoother
+    set-up (Algorithm 1 row by row) on `workers` processes, then `solves` PCG solves timed one by
+    one on one core."""
+    import multiprocessing as mp
+    from oracle import blocks as bk
     from oracle import pum as opum
     from oracle import solver
-    m, levels = 16, 5
-    pr = WORKLOAD
-    f = opum.fourier_source(pin.fourier_coefficients(pr.rhs_seed), pr.rhs_decay)
-    h = opum.build_hierarchy(m, pr.p, pr.equation, levels, f=f, constants=pr.nitsche)
-    st = solver.build_setup(h, k=pr.cheb_k, mode="adaptive", P0=pr.fsai_p0, t_max=pr.t_max, tau=pr.tau)
-    return m, h, st
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(workers) as pool:
+        A, b = _merge(pool.map(_oracle_assemble_strip, [(m, s, pr) for s in _strips(m * m, 4 * workers)]))
+        As, Ps, ms = [A], [], [m]
+        for _ in range(n_levels - 1):
+            P, _ = _merge(pool.map(_oracle_prolong_strip, [(ms[-1], s, pr.p) for s in
+                                                            _strips(ms[-1] ** 2, 4 * workers)]))
+            As.append(bk.galerkin_product(P.transpose(), As[-1], P))
+            Ps.append(P)
+            ms.append(ms[-1] // 2)
+        t1 = time.perf_counter()
+        h = opum.Hierarchy(ms, As, Ps, b, None, [])
 
-
-def oracle_sample(seconds_budget: float = 20.0):
-    """Time the FP64 oracle's PCG (V(3,3), adaptive block-FSAI t_max = 6) on the 16x16-patch
-    version of the workload and scale to the full problem: per-iteration time grows with the
-    number of unknowns (multilevel work is linear in N)."""
-    from oracle import solver
-    pr = WORKLOAD
-    m, h, st = _oracle_setup()
-    t0, c0 = time.perf_counter(), os.times()
-    reps, iters = 0, 0
-    while True:
+        def row_map(fn, rows):
+            rows = list(rows)
+            return pool.map(fn, rows, chunksize=max(1, -(-len(rows) // workers)))
+        st = solver.build_setup(h, k=pr.cheb_k, mode="adaptive", P0=pr.fsai_p0, t_max=pr.t_max, tau=pr.tau,
+                                row_map=row_map)
+    t2 = time.perf_counter()
+    times, iters = [], 0
+    for _ in range(solves):
+        t = time.perf_counter()
         res = solver.solve(st, h.b, rtol=RTOL)
-        reps += 1
-        iters += res.iters
-        if time.perf_counter() - t0 >= seconds_budget:
-            break
-    dt = time.perf_counter() - t0
-    c1 = os.times()
-    busy = (c1.user + c1.system - c0.user - c0.system) / max(dt, 1e-9)  # threads busy on average (BLAS)
-    per_iter_per_dof = dt / iters / (m * m * pr.d)
-    # the oracle's time for the whole workload: per-iteration cost scaled by unknowns (multilevel
-    # work is linear in N) times the sample's own iteration count (nearly size-independent)
-    per_solve_ms = per_iter_per_dof * pr.n_dofs * res.iters * 1e3
-    return per_solve_ms, {"sample": f"oracle FP64 PCG on the 16x16-patch problem (2,560 unknowns, 5 levels, same "
-                                    f"FSAI/smoother settings), {reps} solves of {res.iters} iterations in {dt:.1f} s; "
-                                    f"time per iteration scaled by unknowns to {pr.n_dofs:,} and multiplied by "
-                                    f"{res.iters} iterations",
-                          "cores": max(1, round(busy)), "kind": "oracle",
-                          "cores_note": f"process CPU time / wall time = {busy:.1f} (NumPy/SciPy BLAS threads) of "
-                                        f"{len(os.sched_getaffinity(0))} cores available"}
+        times.append((time.perf_counter() - t) * 1e3)
+        iters = res.iters
+    q.put({"hierarchy_s": t1 - t0, "smoother_setup_s": t2 - t1, "solve_ms": times, "iters": iters})
+
+
+def oracle_run(solves: int, m: int = CPU_SAMPLE_M) -> dict:
+    """Run _oracle_child in a spawned process (one BLAS thread; Algorithm 1's rows over all the
+    host's cores) and return its timings."""
+    import multiprocessing as mp
+    pr = WORKLOAD
+    n_levels = pr.n_levels - (pr.finest_m // m).bit_length() + 1
+    workers = max(1, len(os.sched_getaffinity(0)))
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        ctx = mp.get_context("spawn")
+        q = ctx.Queue()
+        p = ctx.Process(target=_oracle_child, args=(pr, m, n_levels, workers, solves, q))
+        p.start()
+        out = q.get()
+        p.join()
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    out.update(m=m, n_levels=n_levels, unknowns=m * m * pr.d, workers=workers)
+    return out
+
+
+def oracle_baseline(solves: int = 5) -> dict:
+    """cpu_baseline: the FP64 oracle as it stands on the 64 x 64-patch version of the workload
+    (observed, not scaled to the 256 x 256 problem)."""
+    o = oracle_run(solves)
+    value = statistics.mean(o["solve_ms"])
+    return {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+            "sample": f"oracle FP64 PCG (V(3,3), adaptive block-FSAI t_max = 6) on the {o['m']}x{o['m']}-patch "
+                      f"version of the workload ({o['unknowns']:,} unknowns, {o['n_levels']} levels): mean of "
+                      f"{len(o['solve_ms'])} solves of {o['iters']} iterations on one core; observed at this size, "
+                      f"not scaled",
+            "setup_s": {"hierarchy": o["hierarchy_s"], "smoother": o["smoother_setup_s"],
+                        "cores": o["workers"], "note": "assembly, prolongations and Algorithm 1's rows over "
+                                                      f"{o['workers']} processes; Galerkin products and Lanczos on one"},
+            "solve_ms_each": o["solve_ms"]}
 
 
 def run_reference(args):
+    """The reference arm: the oracle on the host cores (the paper ships no code), one PCG solve of
+    the 64 x 64-patch version of the workload per step after an untimed set-up."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        oracle_sample(seconds_budget=0.0)  # one untimed solve each
-    vals, meta = [], None
-    for _ in range(args.steps):
-        v, meta = oracle_sample(seconds_budget=max(2.0, 60.0 / max(args.steps + args.warmup, 1)))
-        vals.append(v)
-    value = statistics.median(vals)
+    o = oracle_run(args.warmup + args.steps, m=getattr(args, "cpu_m", CPU_SAMPLE_M))
+    steps = o["solve_ms"][args.warmup:]
+    value = statistics.mean(steps)
+    sample = (f"oracle FP64 PCG on the {o['m']}x{o['m']}-patch version of the workload ({o['unknowns']:,} unknowns, "
+              f"{o['n_levels']} levels), one solve per step on one core after an untimed set-up")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD.name, "unknowns": WORKLOAD.n_dofs,
-                       "note": "oracle FP64 solve time of the workload from a bounded sample"},
-            "cpu_baseline": dict(meta, value=value, unit=UNIT),
+            "config": {"workload": WORKLOAD.name, "oracle_patches": f"{o['m']}x{o['m']}", "unknowns": o["unknowns"],
+                       "note": "the oracle at the largest size its set-up finishes in about a minute"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1, "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -330,6 +410,106 @@ def measure_anisotropic(ctx, pr, stream, steps):
             "unknowns": m * m * pr.d, "ms_per_solve": ev0.elapsed_time(ev1) / steps, "pcg_iters": rep["iters"]}
 
 
+FP64_PEAK_TFLOPS = 2.0 * 2 * 152 * 2.07e9 / 1e12  # 2 FP64 FMA units' worth per SM per clock (1.26)
+
+
+def timed_solves(H, b, x, stream, n, flexible):
+    """n back-to-back PCG solves bracketed by CUDA events on the library's stream: mean ms."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    reps = [H.pcg(b, x, rtol=RTOL, maxit=200, flexible=flexible) for _ in range(n)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / max(n, 1), reps[-1] if reps else None
+
+
+def setup_roofline(H, ctx, pr, kw):
+    """Set-up of the smoother with the set-up kernels timed (CUDA events on the library's stream):
+    FP64 flops of Algorithm 1's kernel and of the factor kernel per level, from the library's
+    count of the operations performed, over their device time; wall time of the whole set-up."""
+    import torch
+    ctx.timing(True, ["adapt", "factor"])
+    ctx.timing_reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H.setup(**kw)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    kt = ctx.timing_read()
+    ctx.timing(False)
+    fl_a = sum(H.info(l)["flops_adapt"] for l in range(pr.n_levels - 1))
+    fl_f = sum(H.info(l)["flops_factor"] for l in range(pr.n_levels - 1))
+    out = {"wall_s": wall}
+    for name, fl in (("adapt", fl_a), ("factor", fl_f)):
+        n, ms = kt[name]
+        out[name] = {"launches": n, "ms": ms, "gflop": fl / 1e9,
+                     "tflops": (fl / (ms * 1e-3) / 1e12) if ms > 0 else None}
+    a = out["adapt"]
+    out["roofline"] = {"kernel": "Algorithm 1, all steps of all rows, every level (k_adaptive_rows, FP64)",
+                       "bound": "alu", "achieved": a["tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": (a["tflops"] / FP64_PEAK_TFLOPS) if a["tflops"] else None,
+                       "peak_source": "derived: 2 FP64 FMA per SM per clock x 152 SMs x 2.07 GHz"}
+    return out
+
+
+def kernel_table(ctx, H, b, x, steps, ab):
+    ctx.timing(True)
+    ctx.timing_reset()
+    for _ in range(steps):
+        H.pcg(b, x, rtol=RTOL, maxit=200, flexible=True)
+    kt = ctx.timing_read()
+    ctx.timing(False)
+    return kt, {k: {"launches": v[0], "avg_us": (v[1] / v[0] * 1e3) if v[0] else None,
+                    "GBps": (ab[k] / (v[1] / v[0] * 1e-3) / 1e9) if (v[0] and k in ab) else None,
+                    "total_ms_per_solve": v[1] / steps} for k, v in kt.items() if k in ab}
+
+
+def measure_triharmonic(ctx, stream, steps, warmup, peak):
+    """The second workload: triharmonic p = 5 (d = 21) on 256 x 256 patches, 9 levels, nested
+    adaptive block-FSAI (Algorithm 1 from the diagonal, t_max = 6), Chebyshev-4 k = 4, FP32
+    smoothing with BF16 factors on the two finest levels, FP64 outer PCG; and its plain FP64 form."""
+    import torch
+    import paper_2509_06744_gb300 as pum
+    tr = pin.TRIHARMONIC_256
+    b = torch.zeros(tr.n_dofs, dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    H = pum.Hierarchy.assemble(ctx, tr.equation, tr.p, tr.finest_m, tr.n_levels,
+                               f_coef=pin.fourier_coefficients(tr.rhs_seed), f_decay=tr.rhs_decay,
+                               nitsche=tr.nitsche, b=b)
+    torch.cuda.synchronize()
+    t_asm = time.perf_counter() - t0
+    base = dict(p0=tr.fsai_p0, adaptive=tr.adaptive, t_max=tr.t_max, tau=tr.tau, nested=True, k=tr.cheb_k)
+    x = torch.zeros_like(b)
+    su64 = setup_roofline(H, ctx, tr, base)
+    timed_solves(H, b, x, stream, warmup, False)
+    ms64, rep64 = timed_solves(H, b, x, stream, steps, False)
+    x64 = x.clone()
+    su = setup_roofline(H, ctx, tr, dict(base, smooth=tr.smooth_dtype, g=tr.g_dtype, fp32_levels=tr.fp32_levels))
+    timed_solves(H, b, x, stream, warmup, True)
+    ms, rep = timed_solves(H, b, x, stream, steps, True)
+    info = H.info(0)
+    d, N = info["d"], info["n"] * info["d"]
+    ab = {"resid": info["nnzb_A"] * (d * d * 4 + 4) + 3 * N * 4,
+          "resid64": info["nnzb_A"] * (d * d * 8 + 4) + 2 * N * 8 + N * 4,
+          "pcg_ap": info["nnzb_A"] * (d * d * 8 + 4) + 2 * N * 8}
+    kt, table = kernel_table(ctx, H, b, x, steps, ab)
+    r = table["resid"]
+    out = {"workload": tr.name, "unknowns": tr.n_dofs, "ms_per_solve": ms, "pcg_iters": rep["iters"],
+           "fp64_plain": {"ms_per_solve": ms64, "pcg_iters": rep64["iters"]},
+           "rel_diff_vs_fp64_plain": float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64)),
+           "setup_s": {"assembly_and_galerkin": t_asm, "fp64_form": su64["wall_s"], "fp32_form": su["wall_s"]},
+           "setup_kernels": {k: su64[k] for k in ("adapt", "factor")}, "setup_roofline": su64["roofline"],
+           "nested_inner": [H.info(l)["nested_inner"] for l in range(tr.n_levels - 1)],
+           "kernels_finest": table,
+           "roofline": {"kernel": "residual b - A x, finest level, FP32 A (d = 21)", "bound": "hbm",
+                        "achieved": r["GBps"], "peak": peak, "unit": "GB/s", "frac": r["GBps"] / peak,
+                        "algorithmic_bytes_per_launch": ab["resid"], "launches_timed": r["launches"]}}
+    H.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -338,9 +518,10 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the V(2k,0) / Richardson measurements")
-    ap.add_argument("--profile", action="store_true",
-                    help="FP32 form only: one solve bracketed by cudaProfilerStart/Stop (for ncu "
-                         "--profile-from-start off); prints the launch count")
+    ap.add_argument("--no-triharmonic", action="store_true", help="skip the triharmonic workload")
+    ap.add_argument("--profile", choices=["biharmonic", "triharmonic", "setup"], default=None,
+                    help="one FP32-form solve (or one set-up) of that workload bracketed by "
+                         "cudaProfilerStart/Stop (for ncu --profile-from-start off); prints the launch count")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -357,19 +538,27 @@ def main():
 
     import paper_2509_06744_gb300 as pum
 
-    pr = WORKLOAD
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)  # torch ops and the library share one stream
     ctx = pum.Context(local, stream=stream.cuda_stream)
-    N = pr.n_dofs
-    b = torch.zeros(N, dtype=torch.float64, device="cuda")
-    t_setup = time.perf_counter()
     if args.profile:
+        pr = pin.TRIHARMONIC_256 if args.profile == "triharmonic" else WORKLOAD
+        b = torch.zeros(pr.n_dofs, dtype=torch.float64, device="cuda")
         H = pum.Hierarchy.assemble(ctx, pr.equation, pr.p, pr.finest_m, pr.n_levels,
                                    f_coef=pin.fourier_coefficients(pr.rhs_seed), f_decay=pr.rhs_decay,
                                    nitsche=pr.nitsche, b=b)
-        H.setup(p0=pr.fsai_p0, adaptive=pr.adaptive, t_max=pr.t_max, tau=pr.tau, k=pr.cheb_k, smooth="f32",
-                g="f32")
+        kw = dict(p0=pr.fsai_p0, adaptive=pr.adaptive, t_max=pr.t_max, tau=pr.tau, nested=pr.nested, k=pr.cheb_k,
+                  smooth="f32", g=pr.g_dtype if pr.g_dtype != "f64" else "f32",
+                  fp32_levels=pr.fp32_levels)
+        if args.profile == "setup":
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
+            H.setup(**kw)
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+            print(json.dumps({"profile": "one adaptive set-up", "launches": ctx.launches}), flush=True)
+            return
+        H.setup(**kw)
         x = torch.zeros_like(b)
         for _ in range(args.warmup):
             H.pcg(b, x, rtol=RTOL, maxit=200, flexible=True)
@@ -379,43 +568,32 @@ def main():
         rep = H.pcg(b, x, rtol=RTOL, maxit=200, flexible=True)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
-        print(json.dumps({"profile": "one FP32-smoothing PCG solve", "launches": ctx.launches - l0,
+        print(json.dumps({"profile": f"one FP32-form PCG solve, {pr.name}", "launches": ctx.launches - l0,
                           "iters": rep["iters"]}), flush=True)
         return
+
+    pr = WORKLOAD
+    N = pr.n_dofs
+    b = torch.zeros(N, dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
     H = pum.Hierarchy.assemble(ctx, pr.equation, pr.p, pr.finest_m, pr.n_levels,
                                f_coef=pin.fourier_coefficients(pr.rhs_seed), f_decay=pr.rhs_decay,
                                nitsche=pr.nitsche, b=b)
-    t_asm = time.perf_counter() - t_setup
+    torch.cuda.synchronize()
+    t_asm = time.perf_counter() - t0
+    base = dict(p0=pr.fsai_p0, adaptive=pr.adaptive, t_max=pr.t_max, tau=pr.tau, k=pr.cheb_k)
     # plain FP64 form
-    H.setup(p0=pr.fsai_p0, adaptive=pr.adaptive, t_max=pr.t_max, tau=pr.tau, k=pr.cheb_k, smooth="f64")
-    t_fsai = time.perf_counter() - t_setup - t_asm
+    su64 = setup_roofline(H, ctx, pr, dict(base, smooth="f64"))
     x = torch.zeros_like(b)
-
-    def timed_solves(n, flexible):
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = []
-        for _ in range(n):
-            torch.cuda.synchronize()
-            ev0.record(stream)
-            rep = H.pcg(b, x, rtol=RTOL, maxit=200, flexible=flexible)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            reps.append((ev0.elapsed_time(ev1), rep))
-        return reps
-
-    timed_solves(args.warmup, False)
-    plain = timed_solves(args.steps, False)
-    plain_ms = statistics.median(r[0] for r in plain)
-    plain_iters = plain[-1][1]["iters"]
+    timed_solves(H, b, x, stream, args.warmup, False)
+    plain_ms, plain_rep = timed_solves(H, b, x, stream, args.steps, False)
     x64 = x.clone()
-    # headline form: FP32 smoothing with FP64 iterates and residuals, FP64 PCG
-    H.setup(p0=pr.fsai_p0, adaptive=pr.adaptive, t_max=pr.t_max, tau=pr.tau, k=pr.cheb_k, smooth="f32", g="f32")
-    timed_solves(args.warmup, True)
-    # timed region: events around the roofline kernel class only
+    # headline form: FP32 smoothing with FP64 iterates and residuals, FP64 flexible PCG
+    su = setup_roofline(H, ctx, pr, dict(base, smooth="f32", g="f32"))
+    timed_solves(H, b, x, stream, args.warmup, True)
     info = H.info(0)
     roof_tk, roof_desc, roof_profile, roof_sources = ROOFLINE[bool(info["fused_fsai"])]
-    ctx.timing(True, [roof_tk])
-    ctx.timing_reset()
+    # timed region: no kernel instrumentation
     launches0 = ctx.launches
     if world > 1:
         dist.barrier()
@@ -423,56 +601,57 @@ def main():
     with ClockSampler(local) as clk:
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        reps = []
-        for _ in range(args.steps):
-            reps.append(H.pcg(b, x, rtol=RTOL, maxit=200, flexible=True))
+        reps = [H.pcg(b, x, rtol=RTOL, maxit=200, flexible=True) for _ in range(args.steps)]
         ev1.record(stream)
         torch.cuda.synchronize()
     total_ms = ev0.elapsed_time(ev1)
     launches = ctx.launches - launches0
-    kt_live = ctx.timing_read()
     if world > 1:
         total_ms = max_over_ranks(total_ms, "cuda")
     ms_per_solve = total_ms / args.steps
     iters = reps[-1]["iters"]
-    # per-class breakdown from an instrumented repeat of the same solves
-    ctx.timing(True)
+    # the roofline kernel's launch durations: an identical repeat of the timed solves with CUDA
+    # events around that kernel class only (recorded inside the replayed V-cycle graph)
+    ctx.timing(True, [roof_tk])
     ctx.timing_reset()
+    ev0.record(stream)
     for _ in range(args.steps):
         H.pcg(b, x, rtol=RTOL, maxit=200, flexible=True)
-    kt = ctx.timing_read()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    instrumented_ms = ev0.elapsed_time(ev1) / args.steps
+    kt_live = ctx.timing_read()
     ctx.timing(False)
+    ab = algorithmic_bytes(info, 4, 4, 4, 8)
+    kt, kernels = kernel_table(ctx, H, b, x, args.steps, ab)
     # accuracy of the fast form against the plain FP64 solution (equal accuracy check)
     rel_vs_plain = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
     r = torch.zeros_like(b)
     H.residual(0, b, x, r)
     true_rel = float(torch.linalg.norm(r) / torch.linalg.norm(b))
 
-    # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+    # end to end through the C-ABI with host buffers (pinned), copies inside the timed region;
+    # the same statistic as `value`: total time of the timed steps / steps
     b_host = b.cpu().pin_memory()
     x_host = torch.zeros(N, dtype=torch.float64).pin_memory()
     bd, xd = torch.empty_like(b), torch.empty_like(b)
-    e2e = []
-    for i in range(args.warmup + args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+
+    def e2e_step():
         bd.copy_(b_host, non_blocking=True)
         H.pcg(bd, xd, rtol=RTOL, maxit=200, flexible=True)
         x_host.copy_(xd, non_blocking=True)
         stream.synchronize()
-        if i >= args.warmup:
-            e2e.append((time.perf_counter() - t0) * 1e3)
-    e2e_ms = statistics.median(e2e)
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
 
-    # roofline of the FSAI kernel that streams G (the finest-level class with the largest total
-    # time), its launch durations taken live over the timed region
-    ab = algorithmic_bytes(info, 4, 4, 4, 8)
     peak, peak_kind = load_peaks()
     n_l, ms_l = kt_live[roof_tk]
     achieved = ab[roof_tk] / (ms_l / n_l * 1e-3) / 1e9
-    kernels = {k: {"launches": v[0], "avg_us": (v[1] / v[0] * 1e3) if v[0] else None,
-                   "GBps": (ab[k] / (v[1] / v[0] * 1e-3) / 1e9) if v[0] else None,
-                   "total_ms_per_solve": v[1] / args.steps} for k, v in kt.items()}
     dom = max(("resid", "g", "gt", "resid64"), key=lambda k: kt[k][1])
     variants = None
     if not args.no_variants:
@@ -480,13 +659,22 @@ def main():
             variants = measure_variants(H, pr, b, stream, max(3, args.steps // 4))
         except Exception as ex:  # noqa: BLE001
             variants = {"error": f"{type(ex).__name__}: {ex}"}
+    H.close()
+    tri = None
+    if not args.no_triharmonic:
+        try:
+            tri = measure_triharmonic(ctx, stream, max(3, args.steps // 4), args.warmup, peak)
+        except Exception as ex:  # noqa: BLE001
+            tri = {"error": f"{type(ex).__name__}: {ex}"}
 
     if rank != 0:
         return
     cpu = None
     if not args.no_cpu_baseline:
-        v, meta = oracle_sample()
-        cpu = dict(meta, value=v, unit=UNIT)
+        try:
+            cpu = oracle_baseline()
+        except Exception as ex:  # noqa: BLE001
+            cpu = {"error": f"{type(ex).__name__}: {ex}"}
     line = {
         "metric": METRIC, "value": ms_per_solve, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_solve, "higher_is_better": False,
@@ -496,19 +684,25 @@ def main():
                                "residuals and prolongation", "rtol": RTOL,
                    "l2": "working set larger than L2 (no flush)", "parallelism": "replicas only"},
         "pcg_iters": iters, "true_relres": true_rel, "rel_diff_vs_fp64_plain": rel_vs_plain,
-        "fp64_plain": {"ms_per_solve": plain_ms, "pcg_iters": plain_iters, "dtype": "f64"},
-        "setup_s": {"assembly_and_galerkin": t_asm, "fsai_lanczos_fp64": t_fsai},
+        "fp64_plain": {"ms_per_solve": plain_ms, "pcg_iters": plain_rep["iters"], "dtype": "f64"},
+        "setup_s": {"assembly_and_galerkin": t_asm, "fp64_form": su64["wall_s"], "fp32_form": su["wall_s"]},
+        "setup_kernels": {k: su64[k] for k in ("adapt", "factor")},
+        "setup_roofline": su64["roofline"],
         "kernels_finest": kernels,
         "roofline": {"kernel": roof_desc, "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": profiled_traffic(roof_profile, roof_sources),
                      "peak_source": peak_kind, "algorithmic_bytes_per_launch": ab[roof_tk], "launches_timed": n_l,
+                     "timing": "launch durations from an identical repeat of the timed solves with events around "
+                               f"this kernel class only ({instrumented_ms:.3f} ms per solve there)",
                      "largest_total_class": dom},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},
+        "e2e": {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8,
+                "statistic": "mean over the timed steps, as value"},
         "job_solves_per_s": world * args.steps / (total_ms * 1e-3),  # all replicas' solves / slowest rank's time
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "triharmonic": tri,
         "variants": variants,
     }
     print(json.dumps(line), flush=True)

@@ -93,7 +93,11 @@ enum { PUM_P0_LOWER = 0, PUM_P0_DIAG = 1 };
 /* Block-FSAI set-up (Definition 2.2, Algorithm 1, Section 2.2). */
 typedef struct {
   int32_t p0;       /* initial pattern: PUM_P0_LOWER = lower(P(A)), PUM_P0_DIAG = diagonal */
-  int32_t adaptive; /* 0: static pattern P0; 1: Algorithm 1 from P0                       */
+  int32_t adaptive; /* 0: static pattern P0; 1: Algorithm 1 from P0; 2: learned pattern
+                       (the context's pattern model, pum_set_pattern_model) on levels of at
+                       least 1024 block rows, each kept only when it passes the gate against
+                       Algorithm 1 (pum_level_info.learned), Algorithm 1 elsewhere; not with
+                       nested = 1 (PUM_ERR_INVALID_ARG)                                         */
   int32_t t_max;    /* adaptive steps (Algorithm 1)                                        */
   double tau;       /* threshold in (0, 1] (Algorithm 1)                                   */
   int32_t nested;   /* 1: one level of nesting (Section 2.2), same parameters twice        */
@@ -155,6 +159,13 @@ typedef struct {
   int32_t fused_fsai;   /* 1: this level applies G^T G (nested: G1^T G1) reading G once --
                            partial products G_ji^T t_j, then a fixed-order gather (sliced FP32
                            levels; environment PUM_NO_FUSED_FSAI=1 at pum_create turns it off) */
+  double flops_adapt;   /* FP64 flops (2 per multiply-add) of this level's Algorithm 1 kernel
+                           at the last bfsai_setup, counted from the operations it performed  */
+  double flops_factor;  /* FP64 flops of the FSAI factor kernel on the final patterns (from the
+                           pattern sizes: Cholesky s^3/6, solves, S_kk, L_S and G = L_S^-1 F) */
+  int32_t learned;      /* adaptive = 2: 1 when the level kept the learned pattern           */
+  double gate;          /* adaptive = 2: the gate's shortfall (see pum_set_pattern_model); -1
+                           when the level was not scored by the model                         */
 } pum_level_info;
 
 /* Matrices selectable in pum_hier_export. */
@@ -163,7 +174,12 @@ enum { PUM_MAT_A = 0, PUM_MAT_P = 1, PUM_MAT_G = 2, PUM_MAT_GT = 3, PUM_MAT_F0 =
 
 /* ---- context ------------------------------------------------------------------ */
 
-/* Create a context on CUDA device `device`.  cuda_stream is the cudaStream_t the library
+/* Create a context on CUDA device `device`.  Environment switches read here, each "1" to take
+ * effect, for comparisons: PUM_NO_GRAPH (no CUDA graph of the V-cycle), PUM_NO_SELL (no sliced
+ * layouts), PUM_NO_PDL (no programmatic dependent launch), PUM_NO_FUSED_FSAI (two-product FSAI
+ * application), PUM_ADAPT_STEPS (Algorithm 1 with one launch per step and each row's local
+ * systems factored from scratch, instead of one launch that carries every row through all its
+ * steps with an incrementally grown factor).  cuda_stream is the cudaStream_t the library
  * queues all its work on (cudaStreamLegacy, i.e. (void*)1, selects the legacy default
  * stream); NULL makes the library create its own non-blocking stream, in which case the
  * caller must order its own use of the vectors with pum_sync.  Ownership of a passed
@@ -268,19 +284,90 @@ pum_status pum_coarse_solve(pum_ctx *ctx, pum_hier *h, const double *r, double *
 /* z = G^T (G r) for a caller-held block-FSAI factor G (square, block size 3/6/10/15/21) and
  * its explicit block transpose GT, both as DEVICE BSR arrays (on_device = 1, float64,
  * blocks contiguous d x d row-major, columns sorted; the pattern is not re-validated).
- * The paper has no counterpart: this exists for callers that must not allocate device
- * memory -- inside a CUDA graph capture, in a loop that cannot afford the device-wide
- * synchronisation of cudaMalloc/cudaFree, or when all memory is held by another
- * allocator.  It calls no cudaMalloc/cudaFree: the intermediate G r lives in a static
- * device array of 2^20 doubles (8 MiB) held by every GPU that loads the library until
- * exit, so G may have at most 1,048,576 unknowns (larger: PUM_ERR_INVALID_ARG).  The
- * first call on a device looks up that array's device address (with the device
- * current); make that first call before any stream capture.  All calls share the array:
- * calls whose work overlaps on the GPU (other streams or contexts on the same device)
- * race; calls queued on one stream are safe.  r, z: device float64, 16-byte aligned,
- * length n_brows*bs; queued on the context's stream. */
+ * The paper has no counterpart.  It serves callers that cannot allocate device memory:
+ * applications whose device memory is already reserved in full by another allocator (a
+ * framework's caching pool), hosts with a fixed memory budget decided at start-up, and
+ * latency-bound loops that cannot take the device-wide synchronisation cudaFree implies.
+ * It calls no cudaMalloc/cudaFree and no allocating library routine: the intermediate G r
+ * lives in a static device array of 2^20 doubles (8 MiB) that every GPU which loads the
+ * library holds until the process exits, so G may have at most 1,048,576 unknowns (more:
+ * PUM_ERR_INVALID_ARG with a message).  The first call on a device looks that array's
+ * device address up (with the context's device made current for the call; the caller's
+ * current device is restored before returning) and caches it, so make that first call
+ * before any stream capture; a cudaDeviceReset of the device invalidates the cached
+ * address for the rest of the process.  All calls share the array, and every call
+ * overwrites the part it uses before reading it: calls whose work overlaps on the GPU
+ * (other streams, or other contexts on the same device) race on it; calls queued on one
+ * stream are ordered and safe.  r, z and the values: device float64, 8-byte aligned; r and
+ * z of length n_brows*bs; the work is queued on the context's stream. */
 pum_status pum_fsai_apply_noalloc(pum_ctx *ctx, const pum_bsr_view *G, const pum_bsr_view *GT, const double *r,
                                   double *z);
+
+/* ---- learned candidate scoring for the adaptive pattern ------------------------------- */
+/*
+ * Not in the paper: an addition that shortens the set-up of Algorithm 1 (Section 2.1).  A
+ * network scores the candidate blocks of every block row at once; each row takes its t_max
+ * best-scoring candidates.  Candidates of row k: ring 1 = Algorithm 1's admissible set of P0_k
+ * (c < k in the A-rows of P0_k, not in P0_k), ring 2 = the c < k in the A-rows of ring 1 in
+ * neither.  The 12 features per (row, candidate) come from A and the static FSAI G0 on P0 (ring,
+ * direct coupling |A_kc| / sqrt(|A_kk| |A_cc|), first-order gain g_c = |L_c^-1 (G0 A)_kc^T|_F^2
+ * with A_cc = L_c L_c^T (Lemma 2.8's 1 - rho_c to first order), coupling through ring 1, the
+ * rank and share of g_c in the row, the share of P0_k coupled to c, |P0_k|, the grid offset on
+ * assembled hierarchies, the row's fill and its ring-1 size), as float32.
+ * The network: 12 -> 64 -> 64 -> 1 with ReLU; the products use BF16 weights (round to nearest
+ * even of the FP32 master weights) with FP32 accumulation; biases FP32.  Training minimises the
+ * mean binary cross-entropy of the logit against the label "Algorithm 1 chose this candidate"
+ * with Adam (Kingma and Ba 2015) on the device.
+ * The gate (adaptive = 2): on every 16th block row of a level, Algorithm 1 runs as well; with
+ * L the sum of log det S_kk over those rows (Lemma 2.7's measure up to a constant) for the
+ * learned pattern, A1 for Algorithm 1's and P for P0, the shortfall (L - A1) / (P - A1) must be
+ * at most 0.05 (the learned pattern reaches 95% of Algorithm 1's gain), else the level runs
+ * Algorithm 1 on every row.
+ */
+#define PUM_MLP_FEATURES 12
+#define PUM_MLP_HIDDEN 64
+/* Parameters (FP32 master copy), row-major: w1[o][f], w2[o][i]. */
+typedef struct {
+  float w1[PUM_MLP_HIDDEN * PUM_MLP_FEATURES];
+  float b1[PUM_MLP_HIDDEN];
+  float w2[PUM_MLP_HIDDEN * PUM_MLP_HIDDEN];
+  float b2[PUM_MLP_HIDDEN];
+  float w3[PUM_MLP_HIDDEN];
+  float b3;
+} pum_mlp;
+
+/* Candidates of one level (library-owned DEVICE arrays, free with pum_candidates_free):
+ * n candidates, rows ascending, ring 1 then ring 2 within a row (each ascending). */
+typedef struct {
+  int64_t n;
+  int32_t *row, *col;  /* block row and candidate column                                   */
+  float *x;            /* n x PUM_MLP_FEATURES, row-major                                    */
+  float *y;            /* label: 1 when the level's current FSAI pattern holds the candidate */
+} pum_candidates;
+
+/* Candidates, features and labels of a set-up level (non-nested): the pools and features are
+ * those of the hierarchy's P0 (bfsai_params.p0 of the last bfsai_setup), the labels those of
+ * its current pattern (Algorithm 1's after an adaptive set-up).  Synchronous. */
+pum_status pum_fsai_candidates(pum_ctx *ctx, pum_hier *h, int level, pum_candidates *out);
+void pum_candidates_free(pum_candidates *c);
+/* Copy the candidate arrays into caller DEVICE buffers (any may be NULL; row/col n entries,
+ * x n*PUM_MLP_FEATURES, y n), on the context's stream. */
+pum_status pum_candidates_copy(pum_ctx *ctx, const pum_candidates *c, int32_t *row, int32_t *col, float *x, float *y);
+/* logits[i] of the features x[i] (device float32 arrays, n rows). */
+pum_status pum_mlp_forward(pum_ctx *ctx, const pum_mlp *m, const float *x, int64_t n, float *logits);
+/* Mean binary cross-entropy of the logits of x against y (device float32, n rows) and its
+ * gradient with respect to every parameter (host outputs; the BF16 rounding is passed through
+ * as the identity).  Deterministic (fixed-order reductions).  Synchronous. */
+pum_status pum_mlp_grad(pum_ctx *ctx, const pum_mlp *m, const float *x, const float *y, int64_t n, double *loss,
+                        pum_mlp *grad);
+/* Adam on the device from the parameters in *m (updated in place on return): `epochs` passes
+ * over the n samples in a seeded random order (SplitMix64), minibatches of `batch`, step size
+ * lr, beta1 0.9, beta2 0.999, eps 1e-8.  loss (may be NULL): mean loss over all n samples
+ * after training.  Synchronous. */
+pum_status pum_mlp_train(pum_ctx *ctx, pum_mlp *m, const float *x, const float *y, int64_t n, int32_t epochs,
+                         int32_t batch, double lr, uint64_t seed, double *loss);
+/* The model bfsai_setup uses with adaptive = 2 (copied; NULL removes it). */
+pum_status pum_set_pattern_model(pum_ctx *ctx, const pum_mlp *m);
 
 /* ---- inspection, persistence ------------------------------------------------------- */
 
@@ -302,8 +389,11 @@ pum_status pum_hier_destroy(pum_hier *h);
  * stream (inside the captured V-cycle graph when one is used); pum_timing_read returns,
  * per class, the number of launches and the summed event time since the last reset.
  * Class ids: 0 residual b - A x in the smoother's precision, 1 G r, 2 G^T t + Chebyshev
- * update, 3 A p in PCG, 4 residual with the FP64 operator on FP32 vectors. */
-enum { PUM_TK_RESID = 0, PUM_TK_G = 1, PUM_TK_GT = 2, PUM_TK_PCG_AP = 3, PUM_TK_RESID64 = 4, PUM_TK_COUNT = 5 };
+ * update, 3 A p in PCG, 4 residual with the FP64 operator on FP32 vectors; set-up classes
+ * (every level): 5 the Algorithm 1 kernel (all steps of all rows), 6 the FSAI factor
+ * kernel (G on the final patterns). */
+enum { PUM_TK_RESID = 0, PUM_TK_G = 1, PUM_TK_GT = 2, PUM_TK_PCG_AP = 3, PUM_TK_RESID64 = 4, PUM_TK_ADAPT = 5,
+       PUM_TK_FACTOR = 6, PUM_TK_COUNT = 7 };
 #define PUM_TIMING_ALL ((1 << PUM_TK_COUNT) - 1)
 /* mask: bit k times class k (PUM_TIMING_ALL: every class; 0: off).  Timing only the classes
  * of interest keeps the other launches free of event records. */

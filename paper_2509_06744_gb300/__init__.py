@@ -79,7 +79,7 @@ class Context:
         except Exception:
             pass
 
-    TK = {"resid": 0, "g": 1, "gt": 2, "pcg_ap": 3, "resid64": 4}
+    TK = {"resid": 0, "g": 1, "gt": 2, "pcg_ap": 3, "resid64": 4, "adapt": 5, "factor": 6}
 
     def timing(self, enable, classes=None):
         """Enable per-class kernel timing (all classes, or the named ones)."""
@@ -97,12 +97,69 @@ class Context:
         n = (C.c_int64 * _lib.PUM_TK_COUNT)()
         ms = (C.c_double * _lib.PUM_TK_COUNT)()
         self.check(self.lib.pum_timing_read(self.h, n, ms))
-        names = ["resid", "g", "gt", "pcg_ap", "resid64"]
+        names = ["resid", "g", "gt", "pcg_ap", "resid64", "adapt", "factor"]
         return {names[i]: (int(n[i]), float(ms[i])) for i in range(_lib.PUM_TK_COUNT)}
 
     @property
     def launches(self) -> int:
         return int(self.lib.pum_launch_count(self.h))
+
+    # ---- learned candidate scoring (pum_mlp_*; weights as a dict of float32 numpy arrays)
+    def mlp_forward(self, model: dict, x):
+        """Logits of the feature rows x (float32 CUDA tensor, n x 12)."""
+        import torch
+        m = mlp_struct(model)
+        out = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        self.check(self.lib.pum_mlp_forward(self.h, C.byref(m), _fvec(x, "x"), x.shape[0], _fvec(out, "out")))
+        return out
+
+    def mlp_grad(self, model: dict, x, y):
+        m, g, loss = mlp_struct(model), _lib.Mlp(), C.c_double()
+        self.check(self.lib.pum_mlp_grad(self.h, C.byref(m), _fvec(x, "x"), _fvec(y, "y"), x.shape[0],
+                                         C.byref(loss), C.byref(g)))
+        return loss.value, mlp_dict(g)
+
+    def mlp_train(self, model: dict, x, y, epochs=8, batch=8192, lr=3e-3, seed=0):
+        """Adam on the device; returns (trained model, mean loss over all samples)."""
+        m, loss = mlp_struct(model), C.c_double()
+        self.check(self.lib.pum_mlp_train(self.h, C.byref(m), _fvec(x, "x"), _fvec(y, "y"), x.shape[0], epochs,
+                                          batch, lr, seed, C.byref(loss)))
+        return mlp_dict(m), loss.value
+
+    def set_pattern_model(self, model: dict | None):
+        if model is None:
+            self.check(self.lib.pum_set_pattern_model(self.h, None))
+        else:
+            m = mlp_struct(model)
+            self.check(self.lib.pum_set_pattern_model(self.h, C.byref(m)))
+
+
+_MLP_SHAPES = {"w1": (64, 12), "b1": (64,), "w2": (64, 64), "b2": (64,), "w3": (64,), "b3": ()}
+
+
+def mlp_struct(model: dict) -> "_lib.Mlp":
+    m = _lib.Mlp()
+    for name, shape in _MLP_SHAPES.items():
+        v = np.ascontiguousarray(np.asarray(model[name], dtype=np.float32).reshape(shape))
+        if name == "b3":
+            m.b3 = float(v.reshape(-1)[0])
+        else:
+            C.memmove(getattr(m, name), v.ctypes.data, v.nbytes)
+    return m
+
+
+def mlp_dict(m) -> dict:
+    out = {}
+    for name, shape in _MLP_SHAPES.items():
+        out[name] = np.float32(m.b3) if name == "b3" else np.ctypeslib.as_array(getattr(m, name)).reshape(shape).copy()
+    return out
+
+
+def _fvec(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
 
 
 def _bsr_view(indptr, indices, blocks, n_cols):
@@ -241,7 +298,7 @@ class Hierarchy:
     def save(self, path: str):
         self.ctx.check(self.lib.pum_hier_save(self.ctx.h, self.h, path.encode()))
 
-    def setup(self, p0: str = "lower", adaptive: bool = False, t_max: int = 0, tau: float = 1.0,
+    def setup(self, p0: str = "lower", adaptive: bool | int = False, t_max: int = 0, tau: float = 1.0,
               nested: bool = False, tie_rel: float = 1e-9, k: int = 2, lanczos_its: int = 100,
               lanczos_safety: float = 1.01, lanczos_seed: int = 0, smooth: str = "f64", g: str | None = None,
               mixed_levels: int = 64, fp32_levels: int = 64, smoother: str = "cheb4", cycle: str = "vkk"):
@@ -317,6 +374,26 @@ class Hierarchy:
         li = _lib.LevelInfo()
         self.ctx.check(self.lib.pum_level_info_get(self.h, level, C.byref(li)))
         return {f: getattr(li, f) for f, _ in _lib.LevelInfo._fields_}
+
+    def candidates(self, level: int):
+        """Candidates of a set-up level (pum_fsai_candidates), copied into torch CUDA tensors:
+        row, col (int32), x (float32, n x 12), y (float32 labels)."""
+        import torch
+        c = _lib.Candidates()
+        self.ctx.check(self.lib.pum_fsai_candidates(self.ctx.h, self.h, level, C.byref(c)))
+        try:
+            n = int(c.n)
+            row = torch.empty(n, dtype=torch.int32, device="cuda")
+            col = torch.empty(n, dtype=torch.int32, device="cuda")
+            x = torch.empty((n, 12), dtype=torch.float32, device="cuda")
+            y = torch.empty(n, dtype=torch.float32, device="cuda")
+            self.ctx.check(self.lib.pum_candidates_copy(self.ctx.h, C.byref(c), C.c_void_p(row.data_ptr()),
+                                                        C.c_void_p(col.data_ptr()), C.c_void_p(x.data_ptr()),
+                                                        C.c_void_p(y.data_ptr())))
+            self.ctx.sync()
+            return {"row": row, "col": col, "x": x, "y": y}
+        finally:
+            self.lib.pum_candidates_free(C.byref(c))
 
     def export(self, level: int, which: int):
         """Host copy (indptr, indices, blocks) of a level's matrix, float64."""

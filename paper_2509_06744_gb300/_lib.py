@@ -15,7 +15,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NOT_SPD", 5:
 PUM_F64, PUM_F32, PUM_BF16 = 0, 1, 2
 PUM_P0_LOWER, PUM_P0_DIAG = 0, 1
 PUM_MAT_A, PUM_MAT_P, PUM_MAT_G, PUM_MAT_GT, PUM_MAT_F0, PUM_MAT_G1, PUM_MAT_A1 = range(7)
-PUM_TK_COUNT = 5
+PUM_TK_COUNT = 7
 CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream
 
 
@@ -55,7 +55,21 @@ class LevelInfo(C.Structure):
     _fields_ = [("m", c_int32), ("n", c_int32), ("d", c_int32), ("nnzb_A", c_int64), ("nnzb_G", c_int64),
                 ("nnzb_GT", c_int64), ("nnzb_P", c_int64), ("nnzb_F0", c_int64), ("nnzb_G1", c_int64),
                 ("beta", c_double), ("logdet_S", c_double), ("coarsest", c_int32), ("nested_inner", c_int32),
-                ("fused_fsai", c_int32)]
+                ("fused_fsai", c_int32), ("flops_adapt", c_double), ("flops_factor", c_double),
+                ("learned", c_int32), ("gate", c_double)]
+
+
+MLP_FEATURES, MLP_HIDDEN = 12, 64
+
+
+class Mlp(C.Structure):
+    _fields_ = [("w1", C.c_float * (MLP_HIDDEN * MLP_FEATURES)), ("b1", C.c_float * MLP_HIDDEN),
+                ("w2", C.c_float * (MLP_HIDDEN * MLP_HIDDEN)), ("b2", C.c_float * MLP_HIDDEN),
+                ("w3", C.c_float * MLP_HIDDEN), ("b3", C.c_float)]
+
+
+class Candidates(C.Structure):
+    _fields_ = [("n", c_int64), ("row", c_void_p), ("col", c_void_p), ("x", c_void_p), ("y", c_void_p)]
 
 
 P = C.POINTER
@@ -93,6 +107,14 @@ _SIGNATURES = {
     "pum_timing_read": (c_int32, [c_void_p, P(c_int64), P(c_double)]),
     "pum_launch_count": (c_int64, [c_void_p]),
     "pum_fsai_apply_noalloc": (c_int32, [c_void_p, P(BsrView), P(BsrView), c_void_p, c_void_p]),
+    "pum_fsai_candidates": (c_int32, [c_void_p, c_void_p, c_int32, P(Candidates)]),
+    "pum_candidates_free": (None, [P(Candidates)]),
+    "pum_candidates_copy": (c_int32, [c_void_p, P(Candidates), c_void_p, c_void_p, c_void_p, c_void_p]),
+    "pum_mlp_forward": (c_int32, [c_void_p, P(Mlp), c_void_p, c_int64, c_void_p]),
+    "pum_mlp_grad": (c_int32, [c_void_p, P(Mlp), c_void_p, c_void_p, c_int64, P(c_double), P(Mlp)]),
+    "pum_mlp_train": (c_int32, [c_void_p, P(Mlp), c_void_p, c_void_p, c_int64, c_int32, c_int32, c_double,
+                                C.c_uint64, P(c_double)]),
+    "pum_set_pattern_model": (c_int32, [c_void_p, P(Mlp)]),
 }
 
 _LIB = None

@@ -205,8 +205,10 @@ void finalize_smoother(pum_ctx* ctx, pum_hier* h) {
 void check_params(const bfsai_params* fp, const smoother_params* sp) {
   PUM_CHECK(fp && sp, PUM_ERR_INVALID_ARG, "NULL parameters");
   PUM_CHECK(fp->p0 == PUM_P0_LOWER || fp->p0 == PUM_P0_DIAG, PUM_ERR_INVALID_ARG, "p0 must be LOWER or DIAG");
+  PUM_CHECK(fp->adaptive >= 0 && fp->adaptive <= 2, PUM_ERR_INVALID_ARG, "adaptive must be 0, 1 or 2");
   PUM_CHECK(!fp->adaptive || (fp->t_max >= 1 && fp->tau > 0.0 && fp->tau <= 1.0), PUM_ERR_INVALID_ARG,
             "adaptive FSAI needs t_max >= 1 and tau in (0, 1]");
+  PUM_CHECK(!(fp->adaptive == 2 && fp->nested), PUM_ERR_INVALID_ARG, "the learned pattern is not for nested FSAI");
   PUM_CHECK(fp->tie_rel >= 0.0, PUM_ERR_INVALID_ARG, "tie_rel must be >= 0");
   PUM_CHECK(sp->degree_k >= 1 && sp->degree_k <= 64, PUM_ERR_INVALID_ARG, "degree_k must be in 1..64");
   PUM_CHECK(sp->lanczos_its >= 1 && sp->lanczos_safety >= 1.0, PUM_ERR_INVALID_ARG, "Lanczos parameters");
@@ -308,6 +310,8 @@ pum_status pum_create(pum_ctx** out, int device, void* cuda_stream) {
     ctx->pdl = !(np && np[0] == '1');
     const char* nf = getenv("PUM_NO_FUSED_FSAI");
     ctx->fused_fsai = !(nf && nf[0] == '1');
+    const char* as = getenv("PUM_ADAPT_STEPS");
+    ctx->adapt_steps = as && as[0] == '1';
     ctx->status = (DevStatus*)dalloc(sizeof(DevStatus));
     ctx->scal = (double*)dalloc(sizeof(double) * kScalSlots);
     ctx->partials = (double*)dalloc(sizeof(double) * (1 << 16));
@@ -338,6 +342,7 @@ pum_status pum_destroy(pum_ctx* ctx) {
   if (ctx->partials) cudaFree(ctx->partials);
   if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx->model;
   delete ctx;
   return PUM_OK;
 }
@@ -441,6 +446,8 @@ pum_status bfsai_setup(pum_ctx* ctx, pum_hier* h, const bfsai_params* fp, const 
   if (!ctx || !h) return PUM_ERR_INVALID_ARG;
   return guard(ctx, [&]() {
     check_params(fp, sp);
+    PUM_CHECK(fp->adaptive != 2 || ctx->model, PUM_ERR_INVALID_ARG,
+              "adaptive = 2 needs a pattern model (pum_set_pattern_model)");
     PUM_CUDA(cudaStreamSynchronize(ctx->stream));  // no queued kernel may still use what is freed next
     free_smoother(h);
     for (auto& L : h->lv)
@@ -642,6 +649,10 @@ pum_status pum_level_info_get(const pum_hier* h, int level, pum_level_info* info
   info->coarsest = level == (int)h->lv.size() - 1;
   info->nested_inner = L.nested_inner;
   info->fused_fsai = L.gg.S.R > 0 ? 1 : 0;
+  info->flops_adapt = L.flops_adapt;
+  info->flops_factor = L.flops_factor;
+  info->learned = L.learned;
+  info->gate = L.gate;
   return PUM_OK;
 }
 

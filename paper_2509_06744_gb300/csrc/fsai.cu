@@ -302,7 +302,8 @@ __global__ void __launch_bounds__(kFsaiThreads) k_fsai_rows(FsaiArgs a) {
           const double r = rl[q - c0];
           if (r >= 0.0 && r <= thr && (cstar < 0 || a.cci[q] < cstar)) { cstar = a.cci[q]; rstar = r; }
         }
-        choice = (rstar < a.tau) ? cstar : -1;
+        // stop test with the tie band (a gain 1 - rho below tie_rel of tau is rounding)
+        choice = (rstar < a.tau * (1.0 - a.tie_rel)) ? cstar : -1;
       }
       a.chosen[w] = choice;
     }
@@ -454,9 +455,11 @@ void run_rows(pum_ctx* ctx, const Bsr& A, const Pattern& P, const std::vector<in
 }
 
 // Algorithm 1 (or the static pattern when !adaptive); returns the final pattern.
-Pattern fsai_pattern(pum_ctx* ctx, const Bsr& A, const Pattern& P0, const bfsai_params& fp) {
+Pattern fsai_pattern(pum_ctx* ctx, const Bsr& A, const Pattern& P0, const bfsai_params& fp, double* flops) {
   Pattern P = P0;
   if (!fp.adaptive) return P;
+  if (!ctx->adapt_steps && adaptive_patterns_device(ctx, A, P0.rows, fp.t_max, fp.tau, fp.tie_rel, P.rows, flops))
+    return P;
   const int n = A.n_brows;
   std::vector<char> inR(n, 1);
   std::vector<int> mark(n, -1);
@@ -487,24 +490,7 @@ Pattern fsai_pattern(pum_ctx* ctx, const Bsr& A, const Pattern& P0, const bfsai_
     }
     if (rows.empty()) break;
     std::vector<int> chosen;
-    try {
-      run_rows(ctx, A, P, rows, &crp, &cci, fp.tie_rel, fp.tau, &chosen, nullptr, nullptr, nullptr);
-    } catch (const Error& err) {
-      const char* dbg = getenv("PUM_DEBUG_FSAI");
-      if (dbg && dbg[0] == '1') {  // report the patterns of the failing step
-        fprintf(stderr, "fsai step %d failed: %s\n", t, err.msg.c_str());
-        for (size_t w = 0; w < rows.size() && w < 100000; ++w) {
-          const int k = rows[w];
-          if (k > 64) continue;
-          fprintf(stderr, "row %d P:", k);
-          for (int j : P.rows[k]) fprintf(stderr, " %d", j);
-          fprintf(stderr, " C:");
-          for (int q = crp[w]; q < crp[w + 1]; ++q) fprintf(stderr, " %d", cci[q]);
-          fprintf(stderr, "\n");
-        }
-      }
-      throw;
-    }
+    run_rows(ctx, A, P, rows, &crp, &cci, fp.tie_rel, fp.tau, &chosen, nullptr, nullptr, nullptr);
     for (size_t w = 0; w < rows.size(); ++w) {
       const int k = rows[w];
       if (chosen[w] < 0) {
@@ -519,22 +505,98 @@ Pattern fsai_pattern(pum_ctx* ctx, const Bsr& A, const Pattern& P0, const bfsai_
 }
 
 // G (and optionally F) of A on pattern P, FP64; returns sum_k log det S_kk.
-double fsai_factor(pum_ctx* ctx, const Bsr& A, const Pattern& P, Bsr& G, Bsr* F) {
+double fsai_factor(pum_ctx* ctx, const Bsr& A, const Pattern& P, Bsr& G, Bsr* F, double* flops,
+                   std::vector<double>* ld_rows = nullptr) {
   std::vector<int> rp, ci;
   P.to_csr(rp, ci);
   bsr_alloc(G, A.n_brows, A.n_bcols, A.d, PUM_F64, rp, ci);
   if (F) bsr_alloc(*F, A.n_brows, A.n_bcols, A.d, PUM_F64, rp, ci);
   std::vector<int> rows(A.n_brows);
   for (int i = 0; i < A.n_brows; ++i) rows[i] = i;
+  if (flops) {
+    // FP64 multiply-adds per row (s = |P~_k| d): Cholesky s^3/6, Z_k = L^-1 A[P~,k] and the
+    // backward solve s^2 d / 2 each, S_kk s d^2, chol(S_kk) d^3/6, J = L_S^-1 d^3/6, G = J F d^2 (s + d) / 2
+    const double d = A.d;
+    double fma = 0.0;
+    for (const auto& r : P.rows) {
+      const double s = (double)(r.size() - 1) * d;
+      fma += s * s * s / 6.0 + s * s * d + s * d * d + d * d * d / 3.0 + d * d * (s + d) / 2.0;
+    }
+    *flops += 2.0 * fma;
+  }
   double* dld = nullptr;
   PUM_CUDA(cudaMalloc(&dld, sizeof(double) * A.n_brows));
+  timing_begin(ctx, PUM_TK_FACTOR);
   run_rows(ctx, A, P, rows, nullptr, nullptr, 0, 0, nullptr, &G, F, dld);
+  timing_end(ctx, PUM_TK_FACTOR);
   std::vector<double> ld(A.n_brows);
   PUM_CUDA(cudaMemcpy(ld.data(), dld, sizeof(double) * A.n_brows, cudaMemcpyDeviceToHost));
   cudaFree(dld);
   double sum = 0.0;
   for (double v : ld) sum += v;
+  if (ld_rows) *ld_rows = std::move(ld);
   return sum;
+}
+
+// log det S_kk (Definition 2.2) of the given rows for pattern P (the rest of P is not factored).
+std::vector<double> logdet_rows(pum_ctx* ctx, const Bsr& A, const Pattern& P, const std::vector<int>& rows,
+                                double* flops) {
+  std::vector<int> rp, ci;
+  P.to_csr(rp, ci);
+  Bsr G;
+  bsr_alloc(G, A.n_brows, A.n_bcols, A.d, PUM_F64, rp, ci);
+  double* dld = nullptr;
+  PUM_CUDA(cudaMalloc(&dld, sizeof(double) * A.n_brows));
+  run_rows(ctx, A, P, rows, nullptr, nullptr, 0, 0, nullptr, &G, nullptr, dld);
+  std::vector<double> all(A.n_brows), out;
+  PUM_CUDA(cudaMemcpy(all.data(), dld, sizeof(double) * A.n_brows, cudaMemcpyDeviceToHost));
+  cudaFree(dld);
+  bsr_free(G);
+  const double d = A.d;
+  for (int k : rows) {
+    out.push_back(all[k]);
+    const double s = (double)(P.rows[k].size() - 1) * d;
+    if (flops) *flops += 2.0 * (s * s * s / 6.0 + s * s * d + s * d * d + d * d * d / 3.0 + d * d * (s + d) / 2.0);
+  }
+  return out;
+}
+
+constexpr int kLearnedMinRows = 1024;  // smaller levels run Algorithm 1 (cheap there)
+constexpr int kGateStride = 16;        // the gate runs Algorithm 1 on every 16th block row
+constexpr double kGateShortfall = 0.05;
+
+// The learned pattern of a level: the static FSAI G0 on P0 (its per-row log det S_kk into ld0),
+// candidate features, the model's logits, and each row's t_max best-scoring candidates
+// (ties: smaller column).
+Pattern learned_pattern(pum_ctx* ctx, Level& L, const Pattern& P0, const bfsai_params& fp, std::vector<double>& ld0) {
+  Bsr G0;
+  fsai_factor(ctx, L.A, P0, G0, nullptr, &L.flops_factor, &ld0);
+  CandidateSet cs;
+  try {
+    candidates_build(ctx, L.A, G0, P0.rows, L.m, cs);
+  } catch (...) {
+    bsr_free(G0);
+    throw;
+  }
+  bsr_free(G0);
+  std::vector<float> logit(cs.n);
+  float* dl = nullptr;
+  PUM_CUDA(cudaMalloc(&dl, sizeof(float) * std::max<int64_t>(cs.n, 1)));
+  mlp_forward_dev(ctx, *ctx->model, cs.d_x, cs.n, dl);
+  if (cs.n) PUM_CUDA(cudaMemcpy(logit.data(), dl, sizeof(float) * cs.n, cudaMemcpyDeviceToHost));
+  cudaFree(dl);
+  Pattern P = P0;
+  std::vector<std::pair<float, int>> order;
+  for (int k = 0; k < L.n; ++k) {
+    order.clear();
+    for (int q = cs.rp[k]; q < cs.rp[k + 1]; ++q) order.push_back({-logit[q], cs.col[q]});
+    std::sort(order.begin(), order.end());
+    auto& r = P.rows[k];
+    for (int i = 0; i < (int)order.size() && i < fp.t_max; ++i) r.push_back(order[i].second);
+    std::sort(r.begin(), r.end());
+  }
+  candidates_free(cs);
+  return P;
 }
 
 }  // namespace
@@ -546,18 +608,49 @@ void copy_blocks(pum_ctx* ctx, Bsr& dst, const Bsr& src, const int* idx);
 // when the smoother is finalised.
 void fsai_setup_level(pum_ctx* ctx, pum_hier* h, int l) {
   Level& L = h->lv[l];
+  L.flops_adapt = L.flops_factor = 0.0;
   const bfsai_params& fp = h->fp;
   const Pattern P0 = initial_pattern(L.A, fp.p0);
   cudaStream_t s = ctx->stream;
+  L.learned = 0;
+  L.gate = -1.0;
+  if (!fp.nested && fp.adaptive == 2 && ctx->model && L.n >= kLearnedMinRows) {
+    std::vector<double> ld0, ldL;
+    const Pattern P = learned_pattern(ctx, L, P0, fp, ld0);
+    L.logdet_S = fsai_factor(ctx, L.A, P, L.G64, nullptr, &L.flops_factor, &ldL);
+    // the gate: Algorithm 1 on every 16th row, its gain in sum log det S_kk against the learned one
+    std::vector<int> sample;
+    for (int k = 0; k < L.n; k += kGateStride) sample.push_back(k);
+    Pattern Pa = P0;
+    if (!adaptive_patterns_device(ctx, L.A, P0.rows, fp.t_max, fp.tau, fp.tie_rel, Pa.rows, &L.flops_adapt,
+                                  &sample)) {
+      Pa = P0;  // no device instantiation: the step-by-step Algorithm 1 on every row
+      Pa = fsai_pattern(ctx, L.A, P0, bfsai_params{fp.p0, 1, fp.t_max, fp.tau, 0, fp.tie_rel}, &L.flops_adapt);
+    }
+    const std::vector<double> ldA = logdet_rows(ctx, L.A, Pa, sample, &L.flops_factor);
+    double num = 0.0, den = 0.0;
+    for (size_t i = 0; i < sample.size(); ++i) {
+      num += ldL[sample[i]] - ldA[i];
+      den += ld0[sample[i]] - ldA[i];
+    }
+    L.gate = den > 0.0 ? num / den : 0.0;
+    if (L.gate <= kGateShortfall) {
+      L.learned = 1;
+      return;
+    }
+    bsr_free(L.G64);  // the gate failed: Algorithm 1 on every row
+  }
   if (!fp.nested) {
-    const Pattern P = fsai_pattern(ctx, L.A, P0, fp);
-    L.logdet_S = fsai_factor(ctx, L.A, P, L.G64, nullptr);
+    bfsai_params a1 = fp;
+    a1.adaptive = fp.adaptive ? 1 : 0;
+    const Pattern P = fsai_pattern(ctx, L.A, P0, a1, &L.flops_adapt);
+    L.logdet_S = fsai_factor(ctx, L.A, P, L.G64, nullptr, &L.flops_factor);
     return;
   }
   // one level of nesting: A1 = F0 A F0^T, inner FSAI of A1 with the same parameters
-  const Pattern Pout = fsai_pattern(ctx, L.A, P0, fp);
+  const Pattern Pout = fsai_pattern(ctx, L.A, P0, fp, &L.flops_adapt);
   Bsr Gout;
-  fsai_factor(ctx, L.A, Pout, Gout, &L.F064);
+  fsai_factor(ctx, L.A, Pout, Gout, &L.F064, &L.flops_factor);
   bsr_free(Gout);
   Bsr F0T64, FA;
   bsr_transpose(F0T64, L.F064, s);
@@ -570,13 +663,13 @@ void fsai_setup_level(pum_ctx* ctx, pum_hier* h, int l) {
   // directions fall below the rounding of the triple product); the level then uses the inner
   // block Jacobi, G1 = diag_B(G_outer) = S^{-1/2}, which is the non-nested FSAI (Section 2.2).
   try {
-    const Pattern Pin = fsai_pattern(ctx, L.A1, P0, fp);
-    L.logdet_S = fsai_factor(ctx, L.A1, Pin, L.G164, nullptr);
+    const Pattern Pin = fsai_pattern(ctx, L.A1, P0, fp, &L.flops_adapt);
+    L.logdet_S = fsai_factor(ctx, L.A1, Pin, L.G164, nullptr, &L.flops_factor);
     L.nested_inner = 1;
   } catch (const Error& e) {
     if (e.st != PUM_ERR_NOT_SPD) throw;
     Bsr Gout2;
-    L.logdet_S = fsai_factor(ctx, L.A, Pout, Gout2, nullptr);
+    L.logdet_S = fsai_factor(ctx, L.A, Pout, Gout2, nullptr, &L.flops_factor);
     std::vector<int> rp(L.n + 1), ci(L.n);
     for (int i = 0; i < L.n; ++i) { rp[i] = i; ci[i] = i; }
     rp[L.n] = L.n;
@@ -838,3 +931,54 @@ void coarse_factor(pum_ctx* ctx, pum_hier* h) {
 }
 
 }  // namespace pum
+
+// ----------------------------------------------------------------------------- candidates (C-ABI)
+
+extern "C" pum_status pum_fsai_candidates(pum_ctx* ctx, pum_hier* h, int level, pum_candidates* out) {
+  using namespace pum;
+  if (!ctx || !h || !out) return PUM_ERR_INVALID_ARG;
+  *out = pum_candidates{};
+  try {
+    ctx->last_error.clear();
+    PUM_CUDA(cudaSetDevice(ctx->device));
+    PUM_CHECK(h->setup_done, PUM_ERR_INVALID_ARG, "bfsai_setup has not run");
+    PUM_CHECK(!h->fp.nested, PUM_ERR_INVALID_ARG, "candidates of a nested set-up are not supported");
+    PUM_CHECK(level >= 0 && level + 1 < (int)h->lv.size(), PUM_ERR_INVALID_ARG, "level out of range or coarsest");
+    Level& L = h->lv[level];
+    const Pattern P0 = initial_pattern(L.A, h->fp.p0);
+    Bsr G0;
+    fsai_factor(ctx, L.A, P0, G0, nullptr, nullptr);
+    CandidateSet cs;
+    try {
+      candidates_build(ctx, L.A, G0, P0.rows, L.m, cs);
+    } catch (...) {
+      bsr_free(G0);
+      throw;
+    }
+    bsr_free(G0);
+    // labels: membership in the level's current pattern (host copy of G's pattern)
+    const Bsr& G = L.G64;
+    std::vector<float> y(cs.n, 0.0f);
+    for (int k = 0; k < L.n; ++k)
+      for (int q = cs.rp[k]; q < cs.rp[k + 1]; ++q)
+        y[q] = std::binary_search(G.h_col_idx.begin() + G.h_row_ptr[k], G.h_col_idx.begin() + G.h_row_ptr[k + 1],
+                                  cs.col[q])
+                   ? 1.0f
+                   : 0.0f;
+    float* dy = nullptr;
+    PUM_CUDA(cudaMalloc(&dy, sizeof(float) * std::max<int64_t>(cs.n, 1)));
+    if (cs.n) PUM_CUDA(cudaMemcpy(dy, y.data(), sizeof(float) * cs.n, cudaMemcpyHostToDevice));
+    out->n = cs.n;
+    out->row = cs.d_row;
+    out->col = cs.d_col;
+    out->x = cs.d_x;
+    out->y = dy;
+    return PUM_OK;
+  } catch (const Error& e) {
+    ctx->last_error = e.msg;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    ctx->last_error = "host allocation failed";
+    return PUM_ERR_OOM;
+  }
+}

@@ -162,6 +162,9 @@ struct Level {
   Bsr G1, G1T;          // nested: inner G
   double beta = 0.0;
   double logdet_S = 0.0;
+  double flops_adapt = 0.0, flops_factor = 0.0;  // FP64 flops of this level's set-up kernels
+  int learned = 0;      // adaptive = 2: the level kept the learned pattern
+  double gate = -1.0;   // adaptive = 2: the gate's shortfall (-1: not scored by the model)
   int nested_inner = 0;  // nested level: 1 inner FSAI of A1, 0 inner block Jacobi
   // work vectors in the smoothing precision
   void *x = nullptr, *b = nullptr, *r = nullptr, *p = nullptr, *t = nullptr, *u = nullptr;
@@ -240,6 +243,8 @@ struct pum_ctx {
   bool sell = true;                                     // sliced layouts on large levels
   bool pdl = true;                                      // programmatic dependent launch of the cycle's kernels
   bool fused_fsai = true;                               // G read once per FSAI application on sliced levels
+  bool adapt_steps = false;                             // Algorithm 1 step by step (one launch per step)
+  pum_mlp* model = nullptr;                             // candidate-scoring network (adaptive = 2)
 };
 
 namespace pum {
@@ -285,6 +290,26 @@ void build_prolongation(pum_ctx* ctx, int m_f, int p, int q, Level& fine);
 
 // FSAI set-up (fsai.cu)
 void fsai_setup_level(pum_ctx* ctx, pum_hier* h, int l);
+// Learned candidate scoring (learned.cu).  Candidate pools of P0 (ring 1, ring 2) with their
+// features, on the device; logits of a model; FP64 per-row log det S_kk of a factor pass.
+struct CandidateSet {
+  int64_t n = 0;
+  std::vector<int> rp, col;    // host: per-row offsets (n_rows + 1) and columns
+  int* d_row = nullptr;        // device copies
+  int* d_col = nullptr;
+  float* d_x = nullptr;        // n x 12 features
+};
+void candidates_build(pum_ctx* ctx, const Bsr& A, const Bsr& G0, const std::vector<std::vector<int>>& P0, int m,
+                      CandidateSet& cs);
+void candidates_free(CandidateSet& cs);
+void mlp_forward_dev(pum_ctx* ctx, const pum_mlp& m, const float* x, int64_t n, float* logits);
+// Algorithm 1's final patterns for every block row, one CTA per row through all steps (adapt.cu);
+// false when the block size has no instantiation.
+// fp64_flops (may be null) accumulates the kernel's FP64 flops (2 per multiply-add).
+// work_rows (may be null): only these rows run Algorithm 1; the others of `rows` keep P0.
+bool adaptive_patterns_device(pum_ctx* ctx, const Bsr& A, const std::vector<std::vector<int>>& P0, int t_max,
+                              double tau, double tie_rel, std::vector<std::vector<int>>& rows, double* fp64_flops,
+                              const std::vector<int>* work_rows = nullptr);
 void lanczos_level(pum_ctx* ctx, pum_hier* h, int l);
 void coarse_factor(pum_ctx* ctx, pum_hier* h);
 

@@ -59,19 +59,28 @@ def test_roofline_bytes_of_the_finest_level(fused, kernel, expected):
 
 
 def test_reference_arm_prints_the_contract_line(capsys, monkeypatch):
-    """The reference arm (the oracle on the host cores) prints one JSON line with the metric,
-    a cpu_baseline describing the sample and an e2e entry without host-device copies."""
+    """The reference arm (the oracle on the host cores, here on the 8x8-patch version of the
+    workload) prints one JSON line with the metric, a cpu_baseline describing the sample and an
+    e2e entry without host-device copies."""
     import argparse
     import json
     monkeypatch.delenv("RANK", raising=False)
-    real = bench.oracle_sample
-    monkeypatch.setattr(bench, "oracle_sample", lambda seconds_budget=0.0: real(seconds_budget=0.0))
-    bench.run_reference(argparse.Namespace(steps=1, warmup=0, gpus=1, impl="reference"))
+    bench.run_reference(argparse.Namespace(steps=2, warmup=1, gpus=1, impl="reference", cpu_m=8))
     lines = [line for line in capsys.readouterr().out.splitlines() if line.strip()]
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
     assert d["value"] > 0 and d["higher_is_better"] is False
+    assert d["config"]["oracle_patches"] == "8x8" and d["steps"] == 2
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_oracle_sample_is_observed_at_its_own_size():
+    """The oracle's timings come from solves of the sample problem itself (PCG to 1e-8 with the
+    workload's smoother settings), with the set-up timed apart."""
+    o = bench.oracle_run(2, m=8)
+    assert o["m"] == 8 and o["n_levels"] == 4 and o["unknowns"] == 640
+    assert len(o["solve_ms"]) == 2 and all(t > 0 for t in o["solve_ms"])
+    assert 0 < o["iters"] < 50 and o["hierarchy_s"] > 0 and o["smoother_setup_s"] > 0

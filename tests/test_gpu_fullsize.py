@@ -119,6 +119,32 @@ def test_adaptive_fsai_rows_at_full_size(gpu, exported):
             assert np.max(np.abs(G.block(k, j) - v)) <= TOL_FSAI * scale
 
 
+def test_adaptive_fsai_one_launch_equals_step_launches(gpu):
+    """Algorithm 1 carried through all steps per row in one launch (incrementally grown local
+    factors) gives, on every level of the 256x256 hierarchy, the patterns of the step-by-step
+    form (every row's local systems factored from scratch each step), bit for bit, and factors
+    within the FSAI tolerance."""
+    import os
+    L, ctx, H, b = gpu
+    H.setup(p0="lower", adaptive=True, t_max=PR.t_max, tau=PR.tau, k=PR.cheb_k)
+    one = [from_export(H.export(l, L.PUM_MAT_G)) for l in range(PR.n_levels - 1)]
+    os.environ["PUM_ADAPT_STEPS"] = "1"
+    try:
+        c2 = L.Context(0)
+    finally:
+        os.environ.pop("PUM_ADAPT_STEPS", None)
+    b2 = b.clone()
+    H2 = L.Hierarchy.assemble(c2, PR.equation, PR.p, M, PR.n_levels, f_coef=pin.fourier_coefficients(PR.rhs_seed),
+                              f_decay=PR.rhs_decay, nitsche=PR.nitsche, b=b2)
+    H2.setup(p0="lower", adaptive=True, t_max=PR.t_max, tau=PR.tau, k=PR.cheb_k)
+    for l in range(PR.n_levels - 1):
+        ref = from_export(H2.export(l, L.PUM_MAT_G))
+        assert np.array_equal(one[l].indptr, ref.indptr) and np.array_equal(one[l].indices, ref.indices), l
+        assert np.max(np.abs(one[l].blocks - ref.blocks)) <= TOL_FSAI * np.max(np.abs(ref.blocks))
+    H2.close()
+    c2.close()
+
+
 def test_vcycle_symmetric_and_pcg_forms_agree(gpu):
     """At full size: the FP64 cycle is symmetric; FP64 and FP32 forms reach 1e-8 with equal solutions."""
     import torch
@@ -234,3 +260,29 @@ def test_triharmonic_fp32_bf16_form_converges(tri):
     # ~5e-2 of |b| here, agreement to 1e-3 is what 1e-8 recursive residuals can promise (measured:
     # 8e-5), while a wrong cycle would differ by O(1).
     assert float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64)) <= 1e-3
+
+
+def test_triharmonic_nested_coarse_levels_match_oracle(tri):
+    """The nested FSAI (Section 2.2, Algorithm 1 from the diagonal) on the coarse Galerkin levels
+    of the 256x256 triharmonic hierarchy against the oracle's whole-hierarchy run
+    (tests/golden/triharmonic256_nested_coarse.json, written by make_triharmonic_nested_coarse.py):
+    outer and inner patterns bit-exact, the same levels falling back to block Jacobi where A_1 is
+    not numerically SPD (reading R21), sum log det S_kk and the row norms of G_1 within the FSAI
+    tolerance."""
+    import json
+    import os
+    L, ctx, H, b, _ = tri
+    path = os.path.join(os.path.dirname(__file__), "golden", "triharmonic256_nested_coarse.json")
+    gold = json.load(open(path))["levels"]
+    for lev, g in sorted(gold.items(), key=lambda kv: int(kv[0])):
+        lev = int(lev)
+        info = H.info(lev)
+        assert info["n"] == g["n"] and info["nnzb_A"] == g["nnzb_A"], lev
+        assert info["nested_inner"] == g["nested_inner"], f"level {lev}: inner FSAI formed or not"
+        F0 = from_export(H.export(lev, L.PUM_MAT_F0))
+        assert F0.indptr.tolist() == g["F0_indptr"] and F0.indices.tolist() == g["F0_indices"], f"P(F0), level {lev}"
+        G1 = from_export(H.export(lev, L.PUM_MAT_G1))
+        assert G1.indptr.tolist() == g["G1_indptr"] and G1.indices.tolist() == g["G1_indices"], f"P(G1), level {lev}"
+        assert abs(info["logdet_S"] - g["logdet_S"]) <= TOL_FSAI * abs(g["logdet_S"]), lev
+        fro = np.array([np.sqrt(np.sum(G1.blocks[G1.indptr[i]:G1.indptr[i + 1]] ** 2)) for i in range(G1.n_rows)])
+        assert np.max(np.abs(fro - np.array(g["G1_row_fro"])) / np.array(g["G1_row_fro"])) <= TOL_FSAI, lev

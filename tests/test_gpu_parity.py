@@ -690,7 +690,9 @@ def test_kernel_timing_counts_every_finest_launch(lib, small_biharmonic, graph):
     # k-1 FP32 residuals in each smoother
     assert kt["g"][0] == 2 * k * cycles and kt["gt"][0] == 2 * k * cycles
     assert kt["resid64"][0] == 2 * cycles and kt["resid"][0] == 2 * (k - 1) * cycles
-    assert kt["pcg_ap"][0] == rep["iters"] and all(v[1] > 0 for v in kt.values())
+    assert kt["pcg_ap"][0] == rep["iters"]
+    assert all(kt[c][1] > 0 for c in ("resid", "g", "gt", "pcg_ap", "resid64"))
+    assert kt["adapt"][0] == 0 and kt["factor"][0] == 0  # set-up classes: no launch in a solve
     # with only the G^T class selected, the other classes record nothing
     assert kt_gt["gt"][0] == kt["gt"][0] and all(kt_gt[n][0] == 0 for n in ("resid", "g", "pcg_ap", "resid64"))
 
