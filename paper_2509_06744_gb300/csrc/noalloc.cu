@@ -1,20 +1,21 @@
 // Block-FSAI application z = G^T (G r) that allocates no memory.
 //
-// Callers that cannot allocate device memory -- code that runs while a CUDA graph is
-// being captured (a cudaMalloc there breaks or invalidates the capture), host threads of
-// a latency-bound loop that must never hit the device-wide synchronisation of
-// cudaMalloc/cudaFree, or applications whose memory is entirely reserved by another
-// allocator -- still need the intermediate vector t = G r.  Here it lives in one
-// file-scope device array, kNoAllocMaxUnknowns doubles (8 MiB), that every GPU which
-// loads the library holds until the process exits.
+// Some callers cannot allocate device memory: an application whose device memory is
+// already reserved in full by another allocator (a framework's caching pool), a host with
+// a fixed memory budget decided at start-up, or a latency-bound loop that cannot take the
+// device-wide synchronisation that cudaFree implies.  They still need the intermediate
+// vector t = G r.  Here it lives in one file-scope device array, kNoAllocMaxUnknowns
+// doubles (8 MiB), that every GPU which loads the library holds until the process exits.
 //
 // The array's name in host code is only a host-side stand-in, never a device address:
 // its device address is looked up once per device with cudaGetSymbolAddress (on the
 // first call on that device, with that device current) and passed to the kernels.
 // All calls share the array, so calls whose work overlaps on the GPU (different
 // streams, or several contexts on one device) race on it; calls queued on one stream
-// are ordered and safe.  t is fully overwritten by every call, so nothing needs clearing.
+// are ordered and safe.  t is fully overwritten by every call before it is read, so
+// nothing needs clearing.
 #include <mutex>
+#include <string>
 
 #include "pum_internal.cuh"
 
@@ -97,27 +98,40 @@ extern "C" pum_status pum_fsai_apply_noalloc(pum_ctx* ctx, const pum_bsr_view* G
     ctx->last_error = "pum_fsai_apply_noalloc: more than 1048576 unknowns (the static scratch limit)";
     return PUM_ERR_INVALID_ARG;
   }
-  if (((uintptr_t)r & 15) || ((uintptr_t)z & 15) || ((uintptr_t)G->vals & 15) || ((uintptr_t)GT->vals & 15)) {
-    ctx->last_error = "pum_fsai_apply_noalloc: vectors and values must be 16-byte aligned";
+  // the kernels read float64 scalars: 8-byte alignment is what they need
+  if (((uintptr_t)r & 7) || ((uintptr_t)z & 7) || ((uintptr_t)G->vals & 7) || ((uintptr_t)GT->vals & 7)) {
+    ctx->last_error = "pum_fsai_apply_noalloc: vectors and values must be 8-byte aligned";
     return PUM_ERR_INVALID_ARG;
   }
-  if (ctx->device < 0 || ctx->device >= kMaxDevices) return PUM_ERR_INVALID_ARG;
-  cudaError_t e = cudaSetDevice(ctx->device);
-  double* t = nullptr;
-  if (e == cudaSuccess) e = scratch_for(ctx->device, &t);
-  if (e != cudaSuccess) {
-    ctx->last_error = "pum_fsai_apply_noalloc: device scratch lookup failed";
-    return PUM_ERR_CUDA;
-  }
-  if (!launch_any(*G, r, t, ctx->stream)) {
+  if (G->bs != 3 && G->bs != 6 && G->bs != 10 && G->bs != 15 && G->bs != 21) {
     ctx->last_error = "pum_fsai_apply_noalloc: block size must be 3, 6, 10, 15 or 21";
     return PUM_ERR_UNSUPPORTED;
   }
-  launch_any(*GT, t, z, ctx->stream);
-  ctx->launches += 2;
-  if (cudaGetLastError() != cudaSuccess) {
-    ctx->last_error = "pum_fsai_apply_noalloc: kernel launch failed";
-    return PUM_ERR_CUDA;
+  if (ctx->device < 0 || ctx->device >= kMaxDevices) {
+    ctx->last_error = "pum_fsai_apply_noalloc: device ordinal outside [0, 64)";
+    return PUM_ERR_INVALID_ARG;
   }
-  return PUM_OK;
+  // the lookup and the launches run with the context's device current; the caller's
+  // current device is put back on every path out
+  int prev = -1;
+  cudaError_t e = cudaGetDevice(&prev);
+  if (e == cudaSuccess && prev != ctx->device) e = cudaSetDevice(ctx->device);
+  double* t = nullptr;
+  if (e == cudaSuccess) e = scratch_for(ctx->device, &t);
+  pum_status st = PUM_OK;
+  if (e != cudaSuccess) {
+    ctx->last_error = std::string("pum_fsai_apply_noalloc: device scratch lookup failed: ") + cudaGetErrorString(e);
+    st = PUM_ERR_CUDA;
+  } else {
+    launch_any(*G, r, t, ctx->stream);
+    launch_any(*GT, t, z, ctx->stream);
+    ctx->launches += 2;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      ctx->last_error = std::string("pum_fsai_apply_noalloc: kernel launch failed: ") + cudaGetErrorString(e);
+      st = PUM_ERR_CUDA;
+    }
+  }
+  if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+  return st;
 }
