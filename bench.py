@@ -510,6 +510,80 @@ def measure_triharmonic(ctx, stream, steps, warmup, peak):
     return out
 
 
+def measure_learned(ctx, stream, steps, warmup):
+    """The learned candidate scoring (not in the paper; Algorithm 1 stays the fallback and judge):
+    trained on the device on Algorithm 1's choices for the 128x128 and 192x192-patch biharmonic
+    matrices (levels with at least 1,024 block rows), evaluated on the 256x256 workload and on
+    512x512 patches (2.6M unknowns, 10 levels): set-up time, the gate per level, the V-cycle
+    convergence factor rho_A (FP64 form, 6 cycles from a U(-1,1) error) and PCG time to 1e-8 in
+    the FP32 form, each against Algorithm 1's set-up."""
+    import torch
+    import paper_2509_06744_gb300 as pum
+    pr = WORKLOAD
+    out = {}
+
+    def assemble(m, levels):
+        b = torch.zeros(m * m * pr.d, dtype=torch.float64, device="cuda")
+        H = pum.Hierarchy.assemble(ctx, pr.equation, pr.p, m, levels, f_coef=pin.fourier_coefficients(pr.rhs_seed),
+                                   f_decay=pr.rhs_decay, nitsche=pr.nitsche, b=b)
+        return H, b
+    base = dict(p0=pr.fsai_p0, t_max=pr.t_max, tau=pr.tau, k=pr.cheb_k)
+    xs, ys = [], []
+    t0 = time.perf_counter()
+    for m, levels in ((128, 8), (192, 7)):
+        H, _ = assemble(m, levels)
+        H.setup(adaptive=True, **base)
+        for l in range(levels - 1):
+            if H.info(l)["n"] >= 1024:
+                c = H.candidates(l)
+                xs.append(c["x"])
+                ys.append(c["y"])
+        H.close()
+    x, y = torch.cat(xs).contiguous(), torch.cat(ys).contiguous()
+    t_data = time.perf_counter() - t0
+    model0 = pum.init_mlp(1)
+    loss0, _ = ctx.mlp_grad(model0, x, y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    model, loss = ctx.mlp_train(model0, x, y, epochs=20, batch=8192, lr=3e-3, seed=5)
+    t_train = time.perf_counter() - t0
+    out["train"] = {"samples": int(x.shape[0]), "positive_share": float(y.mean()), "matrices": "128x128, 192x192",
+                    "data_s": t_data, "train_s": t_train, "epochs": 20, "batch": 8192, "loss_initial": loss0,
+                    "loss_trained": loss}
+    ctx.set_pattern_model(model)
+    for m, levels in ((256, 9), (512, 10)):
+        H, b = assemble(m, levels)
+        e0 = torch.tensor(pin.uniform_vector(b.numel(), 5), dtype=torch.float64, device="cuda")
+        res = {"unknowns": b.numel(), "levels": levels}
+        for name, adaptive in (("algorithm1", 1), ("learned", 2)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            H.setup(adaptive=adaptive, smooth="f64", **base)
+            torch.cuda.synchronize()
+            t_setup = time.perf_counter() - t0
+            rho = H.convergence_factor(e0, 6)
+            logdet = sum(H.info(l)["logdet_S"] for l in range(levels - 1))
+            gates = [(H.info(l)["gate"], H.info(l)["learned"]) for l in range(levels - 1)]
+            H.setup(adaptive=adaptive, smooth="f32", g="f32", **base)
+            xx = torch.zeros_like(b)
+            timed_solves(H, b, xx, stream, warmup, True)
+            ms, rep = timed_solves(H, b, xx, stream, steps, True)
+            res[name] = {"setup_s_fp64_form": t_setup, "rho_A": rho, "sum_logdet_S": logdet,
+                         "pcg_ms": ms, "pcg_iters": rep["iters"]}
+            if adaptive == 2:
+                res[name]["gate_per_level"] = [{"level": l, "shortfall": g, "kept": k} for l, (g, k) in enumerate(gates)
+                                               if g >= 0.0]
+        a, lrn = res["algorithm1"], res["learned"]
+        res["rho_A_ratio"] = lrn["rho_A"] / a["rho_A"]
+        res["accepted"] = bool(abs(res["rho_A_ratio"] - 1.0) <= 0.05 and
+                               all(g["shortfall"] <= 0.05 for g in lrn.get("gate_per_level", [])))
+        res["setup_speedup"] = a["setup_s_fp64_form"] / lrn["setup_s_fp64_form"]
+        out[f"eval_{m}x{m}"] = res
+        H.close()
+    ctx.set_pattern_model(None)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -519,6 +593,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the V(2k,0) / Richardson measurements")
     ap.add_argument("--no-triharmonic", action="store_true", help="skip the triharmonic workload")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-pattern measurements")
     ap.add_argument("--profile", choices=["biharmonic", "triharmonic", "setup"], default=None,
                     help="one FP32-form solve (or one set-up) of that workload bracketed by "
                          "cudaProfilerStart/Stop (for ncu --profile-from-start off); prints the launch count")
@@ -660,6 +735,12 @@ def main():
         except Exception as ex:  # noqa: BLE001
             variants = {"error": f"{type(ex).__name__}: {ex}"}
     H.close()
+    lrn = None
+    if not args.no_learned:
+        try:
+            lrn = measure_learned(ctx, stream, max(3, args.steps // 4), args.warmup)
+        except Exception as ex:  # noqa: BLE001
+            lrn = {"error": f"{type(ex).__name__}: {ex}"}
     tri = None
     if not args.no_triharmonic:
         try:
@@ -703,6 +784,7 @@ def main():
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "triharmonic": tri,
+        "learned_pattern": lrn,
         "variants": variants,
     }
     print(json.dumps(line), flush=True)

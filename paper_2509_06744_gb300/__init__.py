@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (PUM_BF16, PUM_F32, PUM_F64, PUM_MAT_A, PUM_MAT_A1, PUM_MAT_F0, PUM_MAT_G, PUM_MAT_G1,
                    PUM_MAT_GT, PUM_MAT_P, PUM_P0_DIAG, PUM_P0_LOWER)
 
-__all__ = ["Context", "Hierarchy", "PumError", "make_workers", "setup_batch", "solve_batch", "PUM_F64", "PUM_F32", "PUM_BF16", "PUM_P0_LOWER", "PUM_P0_DIAG",
+__all__ = ["Context", "Hierarchy", "PumError", "make_workers", "setup_batch", "solve_batch", "init_mlp", "PUM_F64", "PUM_F32", "PUM_BF16", "PUM_P0_LOWER", "PUM_P0_DIAG",
            "PUM_MAT_A", "PUM_MAT_P", "PUM_MAT_G", "PUM_MAT_GT", "PUM_MAT_F0", "PUM_MAT_G1", "PUM_MAT_A1"]
 
 _DT = {"f64": PUM_F64, "f32": PUM_F32, "bf16": PUM_BF16}
@@ -135,6 +135,15 @@ class Context:
 
 
 _MLP_SHAPES = {"w1": (64, 12), "b1": (64,), "w2": (64, 64), "b2": (64,), "w3": (64,), "b3": ()}
+
+
+def init_mlp(seed: int) -> dict:
+    """Initial weights of the candidate-scoring network: He-normal (seeded), zero biases, FP32."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x1EA]))
+    f32 = np.float32
+    return {"w1": (rng.standard_normal((64, 12)) * np.sqrt(2.0 / 12)).astype(f32), "b1": np.zeros(64, f32),
+            "w2": (rng.standard_normal((64, 64)) * np.sqrt(2.0 / 64)).astype(f32), "b2": np.zeros(64, f32),
+            "w3": (rng.standard_normal(64) * np.sqrt(1.0 / 64)).astype(f32), "b3": np.zeros((), f32)}
 
 
 def mlp_struct(model: dict) -> "_lib.Mlp":

@@ -168,7 +168,7 @@ void finalize_smoother(pum_ctx* ctx, pum_hier* h) {
       // is applied through the fused layout when it fits; its two sliced copies are then unused.
       Bsr* fg = h->fp.nested ? &L.G1 : &L.G;
       Bsr* fgt = h->fp.nested ? &L.G1T : &L.GT;
-      if (h->fused_fsai && !fg->empty() && fg->n_brows >= kSellMinRows) gg_build(L.gg, *fg, s, ctx->sm_count);
+      if (h->fused_fsai && !fg->empty() && fg->n_brows >= kSellMinRows) gg_build(ctx, L.gg, *fg);
       for (Bsr* m : {&L.As, &L.G, &L.GT, &L.F0, &L.F0T, &L.G1, &L.G1T, &L.Ps, &L.PTs})
         if (!m->empty() && m->n_brows >= kSellMinRows && !(L.gg.S.R > 0 && (m == fg || m == fgt)))
           sell_build(*m, s, ctx->sm_count);

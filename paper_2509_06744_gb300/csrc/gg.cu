@@ -359,7 +359,16 @@ int gg_occupancy_for(int d, int dt, int R, int P, int ns_max) {
 // threads) multiplies the consumer warps.  Take the R with the most block rows resident per SM
 // (CTAs per SM x R), then the most consumer warps per SM, the largest R on ties.  Returns 0 when
 // no group fits.
-int gg_choose_rows(const Bsr& G, int* ctas_per_sm, int* parts) {
+struct GgConfig {
+  int R = 0, P = 0, occ = 0;
+};
+
+// Candidate group sizes R with their consumer partitions P and CTAs per SM: for every number of
+// resident CTAs per SM, the largest R that reaches it (two buffers of the largest group must stay
+// resident, so R is bounded by shared memory; P is at most kGgMaxParts and the longest row, within
+// 1024 threads).  The first entry is the one with the most block rows resident per SM (CTAs per
+// SM x R), then the most consumer warps, the largest R on ties.
+std::vector<GgConfig> gg_candidates(const Bsr& G) {
   const int n = G.n_brows, d = G.d;
   const int vsize = (int)dt_size(G.dt);
   int max_row = 0;
@@ -367,7 +376,9 @@ int gg_choose_rows(const Bsr& G, int* ctas_per_sm, int* parts) {
   int optin = 0, dev = 0;
   PUM_CUDA(cudaGetDevice(&dev));
   PUM_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  int best_r = 0, best_rows = 0, best_warps = 0, best_occ = 0, best_p = 0;
+  GgConfig best;
+  int best_rows = 0, best_warps = 0;
+  std::vector<GgConfig> by_occ(64);
   for (int R = sell_rows_max(d); R >= 2; --R) {
     if (((size_t)vsize * d * R * d) % 16 != 0) continue;
     if (gg_layout(d, R, max_row, vsize).total + 1024 > (size_t)optin) continue;
@@ -379,14 +390,15 @@ int gg_choose_rows(const Bsr& G, int* ctas_per_sm, int* parts) {
     if (rows > best_rows || (rows == best_rows && warps > best_warps)) {
       best_rows = rows;
       best_warps = warps;
-      best_r = R;
-      best_occ = occ;
-      best_p = P;
+      best = GgConfig{R, P, occ};
     }
+    if (occ < 64 && by_occ[occ].R == 0) by_occ[occ] = GgConfig{R, P, occ};  // R descends: the largest
   }
-  *ctas_per_sm = best_occ;
-  *parts = best_p;
-  return best_r;
+  std::vector<GgConfig> out;
+  if (best.R) out.push_back(best);
+  for (const auto& c : by_occ)
+    if (c.R && c.R != best.R) out.push_back(c);
+  return out;
 }
 
 template <int D, typename MT, typename YT, typename X2T>
@@ -455,14 +467,13 @@ void gg_free(FusedG& F) {
   F.dt = PUM_F32;
 }
 
-void gg_build(FusedG& F, const Bsr& G, cudaStream_t st, int sm_count) {
+namespace {
+
+// The fused layout of G for one group size.
+void gg_build_config(FusedG& F, const Bsr& G, cudaStream_t st, int sm_count, const GgConfig& cfg) {
   gg_free(F);
   const int d = G.d, n = G.n_brows;
-  if (!(d == 3 || d == 6 || d == 10 || d == 15 || d == 21)) return;
-  if (!(G.dt == PUM_F32 || G.dt == PUM_BF16) || G.n_bcols != n || n == 0) return;
-  int ctas_per_sm = 0, parts = 0;
-  const int R = gg_choose_rows(G, &ctas_per_sm, &parts);
-  if (R == 0) return;  // rows too long to keep two groups resident: the two-product form stays
+  const int R = cfg.R;
   std::vector<int> goff;
   sell_build_rows(F.S, G, R, st);
   const int ng = F.S.n_groups;
@@ -493,8 +504,89 @@ void gg_build(FusedG& F, const Bsr& G, cudaStream_t st, int sm_count) {
   F.n = n;
   F.d = d;
   F.dt = G.dt;
-  F.ctas = ctas_per_sm * sm_count;
-  F.parts = parts;
+  F.ctas = cfg.occ * sm_count;
+  F.parts = cfg.P;
+}
+
+template <int D, typename MT>
+void gg_partial_launch(pum_ctx* ctx, const FusedG& F, const float* x) {
+  auto kern = k_gg_partial<D, MT>;
+  allow_max_dynamic_smem((const void*)kern);
+  launch_cycle_kernel(ctx, kern, dim3((unsigned)std::min(F.S.n_groups, F.ctas)), dim3(gg_threads(D, F.S.R, F.parts)),
+                      gg_layout(D, F.S.R, F.S.max_slots, (int)sizeof(MT)).total, F.S.n_groups, F.S.R, F.S.max_slots,
+                      F.S.goff, F.S.cols, (const int*)F.tpos, (const MT*)F.S.vals, x, F.w, ctx->status);
+  count_launch(ctx);
+  PUM_CUDA(cudaGetLastError());
+}
+
+template <int D>
+void gg_partial_launch_dt(pum_ctx* ctx, const FusedG& F, const float* x) {
+  if (F.dt == PUM_BF16) gg_partial_launch<D, __nv_bfloat16>(ctx, F, x);
+  else gg_partial_launch<D, float>(ctx, F, x);
+}
+
+// Mean time of the partial-product kernel of layout F over `reps` launches (after one warm-up).
+float gg_time_partial(pum_ctx* ctx, const FusedG& F, const float* x, int reps) {
+  auto run = [&]() {
+    switch (F.d) {
+      case 3: gg_partial_launch_dt<3>(ctx, F, x); break;
+      case 6: gg_partial_launch_dt<6>(ctx, F, x); break;
+      case 10: gg_partial_launch_dt<10>(ctx, F, x); break;
+      case 15: gg_partial_launch_dt<15>(ctx, F, x); break;
+      default: gg_partial_launch_dt<21>(ctx, F, x); break;
+    }
+  };
+  cudaEvent_t a, b;
+  PUM_CUDA(cudaEventCreate(&a));
+  PUM_CUDA(cudaEventCreate(&b));
+  run();
+  PUM_CUDA(cudaEventRecord(a, ctx->stream));
+  for (int i = 0; i < reps; ++i) run();
+  PUM_CUDA(cudaEventRecord(b, ctx->stream));
+  PUM_CUDA(cudaEventSynchronize(b));
+  float ms = 0.f;
+  PUM_CUDA(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return ms / (float)reps;
+}
+
+}  // namespace
+
+// Fused layout of G with its group size chosen by measurement: every candidate configuration
+// (gg_candidates: the heuristic's choice and the largest R for each number of CTAs per SM) is
+// built and its partial-product kernel timed on the context's stream; the fastest is kept.
+void gg_build(pum_ctx* ctx, FusedG& F, const Bsr& G) {
+  gg_free(F);
+  const int d = G.d, n = G.n_brows;
+  if (!(d == 3 || d == 6 || d == 10 || d == 15 || d == 21)) return;
+  if (!(G.dt == PUM_F32 || G.dt == PUM_BF16) || G.n_bcols != n || n == 0) return;
+  const std::vector<GgConfig> cands = gg_candidates(G);
+  if (cands.empty()) return;  // rows too long to keep two groups resident: the two-product form stays
+  GgConfig best = cands[0];
+  if (cands.size() > 1) {
+    float* x = nullptr;
+    PUM_CUDA(cudaMalloc(&x, sizeof(float) * (size_t)n * d));
+    PUM_CUDA(cudaMemsetAsync(x, 0, sizeof(float) * (size_t)n * d, ctx->stream));
+    float best_ms = 0.f;
+    try {
+      for (size_t i = 0; i < cands.size(); ++i) {
+        gg_build_config(F, G, ctx->stream, ctx->sm_count, cands[i]);
+        const float ms = gg_time_partial(ctx, F, x, 5);
+        if (i == 0 || ms < best_ms) {
+          best_ms = ms;
+          best = cands[i];
+        }
+      }
+    } catch (...) {
+      cudaFree(x);
+      throw;
+    }
+    PUM_CUDA(cudaStreamSynchronize(ctx->stream));
+    cudaFree(x);
+    if (F.S.R == best.R && F.parts == best.P) return;
+  }
+  gg_build_config(F, G, ctx->stream, ctx->sm_count, best);
 }
 
 void gg_apply(pum_ctx* ctx, const FusedG& F, const void* r, int epi, const EpiArgs& e, int tk_g, int tk_gt) {

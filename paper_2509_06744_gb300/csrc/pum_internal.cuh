@@ -104,7 +104,8 @@ struct FusedG {
                         // of G in G^T's block order, -1 for padding
   float* w = nullptr;   // nnzb(G) * d partial products, G^T's block order
 };
-void gg_build(FusedG& F, const Bsr& G, cudaStream_t s, int sm_count);
+// Build the fused layout, its group size chosen by timing the candidates on the context's stream.
+void gg_build(pum_ctx* ctx, FusedG& F, const Bsr& G);
 void gg_free(FusedG& F);
 // Sliced layout (sell.cu): build for a FP32/BF16 matrix; product through it (false: not applicable).
 void sell_build(Bsr& m, cudaStream_t s, int sm_count);
