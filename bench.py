@@ -350,7 +350,8 @@ def measure_variants(H, pr, b, stream, steps):
 def measure_batch(ctx, n_workers: int = 16, rhs: int = 16):
     """The batched uneven workload: 64 biharmonic instances (sides 32/64/96/128, p = 2 or 3, drawn
     by seed 3), adaptive FSAI (t_max = 6), FP32 form, 16 N(0,1) right-hand sides each: 1024 PCG
-    solves to 1e-8, run concurrently by 16 worker contexts and, for comparison, by one."""
+    solves to 1e-8, run concurrently by 16 worker contexts and, for comparison, by one; and with
+    the 16 right-hand sides of each instance solved at once (multi-RHS)."""
     import torch
     import paper_2509_06744_gb300 as pum
     insts = pin.batch_instances()
@@ -377,6 +378,23 @@ def measure_batch(ctx, n_workers: int = 16, rhs: int = 16):
         dt = time.perf_counter() - t0
         res[name] = {"workers": len(ws), "s": dt, "solves_per_s": len(items) / dt,
                      "unknown_solves_per_s": unknowns / dt, "max_iters": max(r["iters"] for r in reps)}
+    # the same 1,024 solves with each instance's 16 right-hand sides in one multi-RHS solve (every
+    # product reads its matrix once for the 16 columns; plain FP32 cycle under FP64 PCG)
+    mitems = []
+    for i, (H, it) in enumerate(zip(Hs, insts)):
+        B = torch.stack([items[i * rhs + r][1] for r in range(rhs)]).contiguous()
+        mitems.append((H, B, torch.zeros_like(B)))
+    torch.cuda.synchronize()
+    pum.solve_batch_multi(workers, mitems[:8], rtol=RTOL, flexible=True)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mreps = pum.solve_batch_multi(workers, mitems, rtol=RTOL, flexible=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    res["multi_rhs"] = {"workers": len(workers), "s": dt, "solves_per_s": len(items) / dt,
+                        "unknown_solves_per_s": unknowns / dt,
+                        "max_iters": max(r["iters"] for rr in mreps for r in rr),
+                        "all_converged": all(r["converged"] for rr in mreps for r in rr)}
     for H in Hs:
         H.close()
     for w in workers:

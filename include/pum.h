@@ -246,6 +246,23 @@ pum_status bicgstab_solve(pum_ctx *ctx, pum_hier *h, const double *b, double *x,
  * double.  Synchronous. */
 pum_status pum_convergence_factor(pum_ctx *ctx, pum_hier *h, const double *e0, int n_cycles, double *rho);
 
+/* ---- several right-hand sides of one problem ------------------------------------------ */
+
+/* nrhs (1..16) right-hand sides at once: B and X are DEVICE float64 blocks, column c of length
+ * N_finest at B + c N (X likewise, overwritten).  Every product of the V(k,k) cycle (Section 5,
+ * Algorithm 3 smoothing) reads its matrix once for all columns (blocks of 4 or 16 columns, the
+ * unused ones zero), and PCG runs for each column in lockstep from x0 = 0 with its own scalars,
+ * stopping each column at ||r_c|| / ||b_c|| <= rtol (a finished column is left as it is).  The
+ * cycle runs in the set-up's precision with FP64 outer PCG; in the FP32 form it is the plain FP32
+ * cycle (every level's iterate and residual in FP32; mixed_levels is not used here), so every
+ * smoothed level must be in one precision (fp32_levels >= n_levels - 1).  Non-nested FSAI and
+ * V(k,k) only (PUM_ERR_UNSUPPORTED otherwise).  reps: nrhs reports; rtol, maxit and flexible are
+ * read from reps[0], hist (if not NULL) from each.  PUM_ERR_NOCONV when a column did not reach
+ * rtol.  Synchronous. */
+pum_status pcg_solve_multi(pum_ctx *ctx, pum_hier *h, int32_t nrhs, const double *B, double *X, pcg_report *reps);
+/* Z = the V(k,k) cycle applied to the nrhs columns of R (device float64 blocks as above). */
+pum_status vcycle_apply_multi(pum_ctx *ctx, pum_hier *h, int32_t nrhs, const double *R, double *Z);
+
 /* ---- batches of independent problems ---------------------------------------------------- */
 
 /* bfsai_setup of n distinct hierarchies with the same parameters, by n_workers host threads,
@@ -265,6 +282,12 @@ pum_status pum_setup_batch(pum_ctx *const *workers, int n_workers, pum_hier *con
 pum_status pum_solve_batch(pum_ctx *const *workers, int n_workers, pum_hier *const *hs, int n,
                            const double *const *b, double *const *x, pcg_report *reps, int method,
                            pum_status *status);
+
+/* pcg_solve_multi on n distinct hierarchies, concurrently as pum_solve_batch: item i solves the
+ * nrhs columns of B[i] into X[i] (device blocks, column c at + c N_i), reports reps[i nrhs + c]
+ * (rtol, maxit and flexible from reps[i nrhs]). */
+pum_status pum_solve_batch_multi(pum_ctx *const *workers, int n_workers, pum_hier *const *hs, int n, int nrhs,
+                                 const double *const *B, double *const *X, pcg_report *reps, pum_status *status);
 
 /* ---- single steps of the hot path (device float64 vectors) ------------------------ */
 

@@ -16,7 +16,7 @@ from . import _lib
 from ._lib import (PUM_BF16, PUM_F32, PUM_F64, PUM_MAT_A, PUM_MAT_A1, PUM_MAT_F0, PUM_MAT_G, PUM_MAT_G1,
                    PUM_MAT_GT, PUM_MAT_P, PUM_P0_DIAG, PUM_P0_LOWER)
 
-__all__ = ["Context", "Hierarchy", "PumError", "make_workers", "setup_batch", "solve_batch", "init_mlp", "PUM_F64", "PUM_F32", "PUM_BF16", "PUM_P0_LOWER", "PUM_P0_DIAG",
+__all__ = ["Context", "Hierarchy", "PumError", "make_workers", "setup_batch", "solve_batch", "solve_batch_multi", "init_mlp", "PUM_F64", "PUM_F32", "PUM_BF16", "PUM_P0_LOWER", "PUM_P0_DIAG",
            "PUM_MAT_A", "PUM_MAT_P", "PUM_MAT_G", "PUM_MAT_GT", "PUM_MAT_F0", "PUM_MAT_G1", "PUM_MAT_A1"]
 
 _DT = {"f64": PUM_F64, "f32": PUM_F32, "bf16": PUM_BF16}
@@ -219,6 +219,27 @@ def setup_batch(workers, hierarchies, **setup_kwargs):
     return [int(v) for v in st]
 
 
+def solve_batch_multi(workers, items, rtol: float = 1e-8, maxit: int = 200, flexible: bool = False):
+    """items: [(Hierarchy, B, X), ...] with B, X float64 CUDA tensors of shape (nrhs, N_i) (the same
+    nrhs for all); each hierarchy solves its columns at once (pcg_solve_multi), the hierarchies
+    concurrently on the workers.  Returns per item a list of report dicts."""
+    n = len(items)
+    nrhs = items[0][1].shape[0]
+    wa = (C.c_void_p * len(workers))(*[w.h for w in workers])
+    ha = (C.c_void_p * n)(*[it[0].h for it in items])
+    ba = (C.c_void_p * n)(*[_vec(it[1], "B").value for it in items])
+    xa = (C.c_void_p * n)(*[_vec(it[2], "X").value for it in items])
+    hists = [(C.c_double * (maxit + 1))() for _ in range(n * nrhs)]
+    reps = (_lib.PcgReport * (n * nrhs))(*[_lib.PcgReport(rtol, maxit, int(flexible), hh, 0, 0, 0.0) for hh in hists])
+    st = (C.c_int32 * n)()
+    rc = workers[0].lib.pum_solve_batch_multi(wa, len(workers), ha, n, nrhs, ba, xa, reps, st)
+    if rc != 0:
+        bad = next((i for i in range(n) if st[i] != 0), None)
+        raise PumError(rc if bad is None else int(st[bad]), f"batch multi-RHS solve (item {bad})")
+    return [[{"iters": reps[i * nrhs + c].iters, "converged": bool(reps[i * nrhs + c].converged)}
+             for c in range(nrhs)] for i in range(n)]
+
+
 def solve_batch(workers, items, rtol: float = 1e-8, maxit: int = 200, flexible: bool = False,
                 method: str = "pcg", allow_noconv=False):
     """items: [(Hierarchy, b, x), ...]; solves them concurrently on the workers' streams (items of
@@ -348,6 +369,22 @@ class Hierarchy:
             self.ctx.check(st)
         return {"iters": rep.iters, "converged": bool(rep.converged), "final_relres": rep.final_relres,
                 "history": [hist[i] for i in range(rep.iters + 1)]}
+
+    def pcg_multi(self, B, X, rtol: float = 1e-8, maxit: int = 200, flexible: bool = False, allow_noconv=False):
+        """PCG for the rows of B (float64 CUDA tensor of shape (nrhs, N), one right-hand side per
+        row) at once into X (same shape); one report dict per right-hand side."""
+        nrhs = B.shape[0]
+        hists = [(C.c_double * (maxit + 1))() for _ in range(nrhs)]
+        reps = (_lib.PcgReport * nrhs)(*[_lib.PcgReport(rtol, maxit, int(flexible), hh, 0, 0, 0.0) for hh in hists])
+        st = self.lib.pcg_solve_multi(self.ctx.h, self.h, nrhs, _vec(B, "B"), _vec(X, "X"), reps)
+        if not (st == 0 or (allow_noconv and st == _lib.PUM_ERR_NOCONV)):
+            self.ctx.check(st)
+        return [{"iters": r.iters, "converged": bool(r.converged), "final_relres": r.final_relres,
+                 "history": [hh[i] for i in range(r.iters + 1)]} for r, hh in zip(reps, hists)]
+
+    def vcycle_multi(self, R, Z):
+        """Z = the V(k,k) cycle applied to every row of R (shape (nrhs, N), float64 CUDA)."""
+        self.ctx.check(self.lib.vcycle_apply_multi(self.ctx.h, self.h, R.shape[0], _vec(R, "R"), _vec(Z, "Z")))
 
     def convergence_factor(self, e0, n_cycles: int) -> float:
         """rho_A of the stationary cycle from the error e0 (the measure of the paper's figures)."""

@@ -115,6 +115,10 @@ _SIGNATURES = {
     "pum_mlp_train": (c_int32, [c_void_p, P(Mlp), c_void_p, c_void_p, c_int64, c_int32, c_int32, c_double,
                                 C.c_uint64, P(c_double)]),
     "pum_set_pattern_model": (c_int32, [c_void_p, P(Mlp)]),
+    "pcg_solve_multi": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p, P(PcgReport)]),
+    "vcycle_apply_multi": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p, c_void_p]),
+    "pum_solve_batch_multi": (c_int32, [P(c_void_p), c_int32, P(c_void_p), c_int32, c_int32, P(c_void_p),
+                                        P(c_void_p), P(PcgReport), P(c_int32)]),
 }
 
 _LIB = None

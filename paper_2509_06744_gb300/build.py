@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpum.so")
-SOURCES = ["bsr.cu", "sell.cu", "gg.cu", "batch.cu", "assemble.cu", "fsai.cu", "adapt.cu", "learned.cu", "solve.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["bsr.cu", "sell.cu", "gg.cu", "batch.cu", "assemble.cu", "fsai.cu", "adapt.cu", "learned.cu", "multi.cu", "solve.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -85,3 +85,15 @@ extern "C" pum_status pum_solve_batch(pum_ctx* const* workers, int n_workers, pu
     return method == 0 ? pcg_solve(ctx, hs[i], b[i], x[i], &reps[i]) : bicgstab_solve(ctx, hs[i], b[i], x[i], &reps[i]);
   });
 }
+
+extern "C" pum_status pum_solve_batch_multi(pum_ctx* const* workers, int n_workers, pum_hier* const* hs, int n,
+                                            int nrhs, const double* const* B, double* const* X, pcg_report* reps,
+                                            pum_status* status) {
+  if (!B || !X || !reps || nrhs < 1) return PUM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < i; ++j)
+      if (hs && hs[i] == hs[j]) return PUM_ERR_INVALID_ARG;  // one multi-solve per hierarchy
+  return run_batch(workers, n_workers, hs, n, status, [&](pum_ctx* ctx, int i) {
+    return pcg_solve_multi(ctx, hs[i], nrhs, B[i], X[i], reps + (size_t)i * nrhs);
+  });
+}
