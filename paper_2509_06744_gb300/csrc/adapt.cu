@@ -490,7 +490,7 @@ bool adaptive_patterns_device(pum_ctx* ctx, const Bsr& A, const std::vector<std:
   a.max_row = std::max(A.max_row_nnzb, 1);
   PUM_CHECK(a.np_cap <= 64, PUM_ERR_UNSUPPORTED, "adaptive FSAI: row pattern longer than 64 blocks");
   // Every tracked column comes from the A-row of a member of P_k (|P_k| <= np_cap + 1), which
-  // bounds the slots a row can need; a first launch uses at most 256 slots per row (enough for
+  // bounds the slots a row can need; a first launch uses at most 128 slots per row (enough for
   // the 3x3 and 5x5 block stencils of the PUM levels) and rows beyond that rerun with the bound.
   const int bound = std::max(1 + np0, std::min(n, 1 + np0 + (a.np_cap + 1) * a.max_row));
   const int64_t sd = (int64_t)a.np_cap * d * d + 3 * d * d + d;
@@ -524,7 +524,7 @@ bool adaptive_patterns_device(pum_ctx* ctx, const Bsr& A, const std::vector<std:
   std::vector<int> hnp(n), hcols((size_t)n * (a.np_cap + 1));
   DevStatus st{};
   for (int attempt = 0; attempt < 2; ++attempt) {
-    a.slots = attempt == 0 ? std::min(bound, 256) : bound;
+    a.slots = attempt == 0 ? std::min(bound, 128) : bound;
     const int ctas = std::max(1, std::min(a.n_work, ctx->sm_count * 4));
     double* slab = nullptr;
     PUM_CUDA(cudaMalloc(&slab, sizeof(double) * (size_t)ctas * a.slots * a.slot_doubles));

@@ -76,6 +76,7 @@ void free_level(Level& L) {
 
 void free_smoother(pum_hier* h) {
   graph_destroy(h->vgraph);
+  multi_cache_free(h->multi);
   for (auto& L : h->lv) {
     for (Bsr* m : {&L.As, &L.PT, &L.Ps, &L.PTs, &L.G, &L.GT, &L.F0, &L.F0T, &L.G1, &L.G1T}) bsr_free(*m);
     for (void** v : {&L.x, &L.b, &L.r, &L.p, &L.t, &L.u, &L.c, &L.e, (void**)&L.b64, (void**)&L.z64, &L.zs})
@@ -795,6 +796,7 @@ pum_status pum_hier_destroy(pum_hier* h) {
   if (!h) return PUM_ERR_INVALID_ARG;
   cudaDeviceSynchronize();  // kernels queued on any stream may still read the hierarchy
   graph_destroy(h->vgraph);
+  multi_cache_free(h->multi);
   for (auto& L : h->lv) free_level(L);
   for (auto& w : h->w64)
     if (w) cudaFree(w);

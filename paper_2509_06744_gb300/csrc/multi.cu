@@ -37,32 +37,71 @@ __device__ __forceinline__ double ld<__nv_bfloat16>(const __nv_bfloat16* p) {
 }
 
 // y (n_rows D x K) by epilogue of acc = M x; MT matrix values, VT vectors (accumulation in VT's
-// precision: FP32 for float vectors, FP64 for double).
+// precision: FP32 for float vectors, FP64 for double).  One warp per block row: the warp loads each
+// block and its panel X_j with coalesced loads into registers one block ahead (the column indices
+// of the row are read up front, 32 at a time, and passed by shuffles), stages them in its shared
+// memory, and every lane then forms its outputs (r, c) from there.
 template <int D, int K, typename MT, typename VT>
 __global__ void __launch_bounds__(128) k_bsr_mm(int n_rows, const int* __restrict__ rp, const int* __restrict__ ci,
                                                 const MT* __restrict__ vals, int stride, const VT* __restrict__ x,
                                                 VT* __restrict__ y, const VT* __restrict__ b, VT* __restrict__ xo,
                                                 int epi, double mu2, double dmu) {
+  static_assert(32 % K == 0, "a lane's column is the same for all its outputs");
   constexpr int kOut = (D * K + 31) / 32;
-  const int row = blockIdx.x * 4 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  constexpr int kM = (D * D + 31) / 32, kX = (D * K + 31) / 32;
+  __shared__ VT sM[4][D * D];
+  __shared__ VT sX[4][D * K];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * 4 + w;
   if (row >= n_rows) return;
+  const int c = lane % K;
   VT acc[kOut];
 #pragma unroll
   for (int q = 0; q < kOut; ++q) acc[q] = VT(0);
-  for (int p = rp[row]; p < rp[row + 1]; ++p) {
+  const int p0 = rp[row], p1 = rp[row + 1];
+  VT mv[kM], xv[kX];
+  int cols = 0;  // lane i holds the column of block p0 + 32 * chunk + i
+  auto fetch = [&](int p) {
+    if (((p - p0) & 31) == 0) cols = (p + lane < p1) ? ci[p + lane] : 0;
+    const int j = __shfl_sync(0xffffffffu, cols, (p - p0) & 31);
     const MT* M = vals + (int64_t)p * stride;
-    const VT* X = x + (int64_t)ci[p] * D * K;
+    const VT* X = x + (int64_t)j * D * K;
+#pragma unroll
+    for (int i = 0; i < kM; ++i) {
+      const int e = lane + 32 * i;
+      mv[i] = e < D * D ? (VT)ld(M + e) : VT(0);
+    }
+#pragma unroll
+    for (int i = 0; i < kX; ++i) {
+      const int e = lane + 32 * i;
+      xv[i] = e < D * K ? X[e] : VT(0);
+    }
+  };
+  if (p0 < p1) fetch(p0);
+  for (int p = p0; p < p1; ++p) {
+#pragma unroll
+    for (int i = 0; i < kM; ++i)
+      if (lane + 32 * i < D * D) sM[w][lane + 32 * i] = mv[i];
+#pragma unroll
+    for (int i = 0; i < kX; ++i)
+      if (lane + 32 * i < D * K) sX[w][lane + 32 * i] = xv[i];
+    __syncwarp();
+    if (p + 1 < p1) fetch(p + 1);  // the next block's loads overlap this block's arithmetic
+    VT xc[D];
+#pragma unroll
+    for (int t = 0; t < D; ++t) xc[t] = sX[w][t * K + c];
 #pragma unroll
     for (int q = 0; q < kOut; ++q) {
       const int e = lane + 32 * q;
       if (e < D * K) {
-        const int r = e / K, c = e - (e / K) * K;
+        const int r = e / K;
         VT a = acc[q];
 #pragma unroll
-        for (int t = 0; t < D; ++t) a = fma((VT)ld(M + r * D + t), X[t * K + c], a);
+        for (int t = 0; t < D; ++t) a = fma(sM[w][r * D + t], xc[t], a);
         acc[q] = a;
       }
     }
+    __syncwarp();
   }
 #pragma unroll
   for (int q = 0; q < kOut; ++q) {
@@ -386,6 +425,11 @@ void cycle_block(pum_ctx* ctx, pum_hier* h, MultiWork& w, const double* r, doubl
   PUM_CUDA(cudaGetLastError());
 }
 
+bool capturable_stream(pum_ctx* ctx) {
+  const uintptr_t st = (uintptr_t)ctx->stream;
+  return ctx->graphs && st > 2;  // not the legacy or per-thread default stream
+}
+
 template <typename F>
 pum_status guarded(pum_ctx* ctx, F&& f) {
   try {
@@ -403,6 +447,80 @@ pum_status guarded(pum_ctx* ctx, F&& f) {
 
 }  // namespace
 
+// Per hierarchy and block width: the cycle's work blocks, the PCG blocks and scalars, and the
+// cycle (r -> z on the cached blocks) captured as a CUDA graph on the first call from a
+// capturable stream, replayed by every later cycle.
+struct MultiCache {
+  MultiWork w;
+  double *x = nullptr, *r = nullptr, *z = nullptr, *zo = nullptr, *p = nullptr, *q = nullptr;
+  double *part = nullptr, *sc = nullptr;
+  int* live = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;
+};
+
+void multi_cache_free(MultiCache*& c) {
+  if (!c) return;
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  delete c;
+  c = nullptr;
+}
+
+namespace {
+
+constexpr int kDotBlocks = 152 * 4;
+
+MultiCache& multi_cache(pum_ctx* ctx, pum_hier* h, int nrhs) {
+  const int K = nrhs <= 4 ? 4 : 16;
+  if (h->multi && h->multi->w.K == K) return *h->multi;
+  multi_cache_free(h->multi);
+  auto c = new MultiCache();
+  try {
+    multi_prepare(ctx, h, c->w, nrhs);
+    const int64_t NK = (int64_t)h->lv[0].n * h->lv[0].d * K;
+    for (double** v : {&c->x, &c->r, &c->z, &c->zo, &c->p, &c->q}) *v = (double*)c->w.alloc(sizeof(double) * NK);
+    c->part = (double*)c->w.alloc(sizeof(double) * kDotBlocks * K);
+    c->sc = (double*)c->w.alloc(sizeof(double) * 6 * K);
+    c->live = (int*)c->w.alloc(sizeof(int) * K);
+  } catch (...) {
+    delete c;
+    throw;
+  }
+  h->multi = c;
+  return *c;
+}
+
+// z = B r on the cache's blocks: replayed from the captured graph where the stream allows it.
+void multi_cycle(pum_ctx* ctx, pum_hier* h, MultiCache& c) {
+  if (!capturable_stream(ctx)) {
+    cycle_block(ctx, h, c.w, c.r, c.z);
+    return;
+  }
+  if (!c.exec) {
+    cudaGraph_t graph = nullptr;
+    const int64_t l0 = ctx->launches;
+    PUM_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    try {
+      cycle_block(ctx, h, c.w, c.r, c.z);
+    } catch (...) {
+      cudaStreamEndCapture(ctx->stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      ctx->launches = l0;
+      throw;
+    }
+    PUM_CUDA(cudaStreamEndCapture(ctx->stream, &graph));
+    c.kernels = ctx->launches - l0;
+    ctx->launches = l0;
+    const cudaError_t e = cudaGraphInstantiate(&c.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    PUM_CUDA(e);
+  }
+  PUM_CUDA(cudaGraphLaunch(c.exec, ctx->stream));
+  ctx->launches += c.kernels;
+}
+
+}  // namespace
+
 }  // namespace pum
 
 using namespace pum;
@@ -411,18 +529,16 @@ extern "C" pum_status vcycle_apply_multi(pum_ctx* ctx, pum_hier* h, int32_t nrhs
   if (!ctx || !h || !R || !Z) return PUM_ERR_INVALID_ARG;
   return guarded(ctx, [&]() {
     check_multi(h, nrhs);
-    MultiWork w;
-    multi_prepare(ctx, h, w, nrhs);
+    MultiCache& c = multi_cache(ctx, h, nrhs);
+    const int K = c.w.K;
     const int64_t N = (int64_t)h->lv[0].n * h->lv[0].d;
-    double* ru = (double*)w.alloc(sizeof(double) * N * w.K);
-    double* zu = (double*)w.alloc(sizeof(double) * N * w.K);
-    k_to_umajor<double, double><<<grid_for(N * w.K), 256, 0, ctx->stream>>>(R, ru, N, w.K, nrhs);
+    k_to_umajor<double, double><<<grid_for(N * K), 256, 0, ctx->stream>>>(R, c.r, N, K, nrhs);
     count_launch(ctx);
-    cycle_block(ctx, h, w, ru, zu);
-    k_to_cmajor<double, double><<<grid_for(N * nrhs), 256, 0, ctx->stream>>>(zu, Z, N, w.K, nrhs);
+    multi_cycle(ctx, h, c);
+    k_to_cmajor<double, double><<<grid_for(N * nrhs), 256, 0, ctx->stream>>>(c.z, Z, N, K, nrhs);
     count_launch(ctx);
     PUM_CUDA(cudaGetLastError());
-    PUM_CUDA(cudaStreamSynchronize(ctx->stream));  // the work blocks are freed on return
+    PUM_CUDA(cudaStreamSynchronize(ctx->stream));
     return PUM_OK;
   });
 }
@@ -436,25 +552,16 @@ extern "C" pum_status pcg_solve_multi(pum_ctx* ctx, pum_hier* h, int32_t nrhs, c
     const double rtol = reps[0].rtol;
     const int flexible = reps[0].flexible;
     PUM_CHECK(maxit >= 1 && rtol > 0.0, PUM_ERR_INVALID_ARG, "multi-RHS: maxit >= 1 and rtol > 0 (from reps[0])");
-    MultiWork w;
-    multi_prepare(ctx, h, w, nrhs);
-    const int K = w.K;
+    MultiCache& c = multi_cache(ctx, h, nrhs);
+    const int K = c.w.K;
     cudaStream_t s = ctx->stream;
     const int64_t N = (int64_t)h->lv[0].n * h->lv[0].d, NK = N * K;
-    double* x = (double*)w.alloc(sizeof(double) * NK);
-    double* r = (double*)w.alloc(sizeof(double) * NK);
-    double* z = (double*)w.alloc(sizeof(double) * NK);
-    double* zo = (double*)w.alloc(sizeof(double) * NK);
-    double* p = (double*)w.alloc(sizeof(double) * NK);
-    double* q = (double*)w.alloc(sizeof(double) * NK);
-    const int nb = 152 * 4;
-    double* part = (double*)w.alloc(sizeof(double) * nb * K);
-    double* sc = (double*)w.alloc(sizeof(double) * 6 * K);  // rz, pq, rr, rz_new, rz_cross, bb
+    double *x = c.x, *r = c.r, *z = c.z, *zo = c.zo, *p = c.p, *q = c.q, *part = c.part, *sc = c.sc;
     double *rz = sc, *pq = sc + K, *rr = sc + 2 * K, *rzn = sc + 3 * K, *rzc = sc + 4 * K, *bb = sc + 5 * K;
-    int* live = (int*)w.alloc(sizeof(int) * K);
+    int* live = c.live;
     auto dots = [&](const double* a, const double* b2, double* out) {
-      k_coldot<<<nb, kDotThreads, 0, s>>>(a, b2, N, K, part);
-      k_coldot_sum<<<1, 32, 0, s>>>(part, nb, K, out);
+      k_coldot<<<kDotBlocks, kDotThreads, 0, s>>>(a, b2, N, K, part);
+      k_coldot_sum<<<1, 32, 0, s>>>(part, kDotBlocks, K, out);
       ctx->launches += 2;
       PUM_CUDA(cudaGetLastError());
     };
@@ -462,19 +569,19 @@ extern "C" pum_status pcg_solve_multi(pum_ctx* ctx, pum_hier* h, int32_t nrhs, c
     count_launch(ctx);
     PUM_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * NK, s));
     dots(r, r, bb);
-    std::vector<double> hbb(K), hrr(K);
+    std::vector<double> hbb(K), hrr(K), hpq(K);
     PUM_CUDA(cudaMemcpyAsync(hbb.data(), bb, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
     PUM_CUDA(cudaStreamSynchronize(s));
     std::vector<int> hlive(K, 0);
-    for (int c = 0; c < nrhs; ++c) {
-      hlive[c] = hbb[c] > 0.0;
-      reps[c].iters = 0;
-      reps[c].converged = !hlive[c];
-      reps[c].final_relres = 0.0;
-      if (reps[c].hist) reps[c].hist[0] = 1.0;
+    for (int cc = 0; cc < nrhs; ++cc) {
+      hlive[cc] = hbb[cc] > 0.0;
+      reps[cc].iters = 0;
+      reps[cc].converged = !hlive[cc];
+      reps[cc].final_relres = 0.0;
+      if (reps[cc].hist) reps[cc].hist[0] = 1.0;
     }
     PUM_CUDA(cudaMemcpyAsync(live, hlive.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
-    cycle_block(ctx, h, w, r, z);
+    multi_cycle(ctx, h, c);  // z = B r
     PUM_CUDA(cudaMemcpyAsync(p, z, sizeof(double) * NK, cudaMemcpyDeviceToDevice, s));
     dots(r, z, rz);
     for (int it = 1; it <= maxit; ++it) {
@@ -487,22 +594,21 @@ extern "C" pum_status pcg_solve_multi(pum_ctx* ctx, pum_hier* h, int32_t nrhs, c
       k_pcg_xr<<<grid_for(NK), 256, 0, s>>>(x, r, p, q, rz, pq, live, N, K);
       count_launch(ctx);
       dots(r, r, rr);
-      std::vector<double> hpq(K);
       PUM_CUDA(cudaMemcpyAsync(hrr.data(), rr, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
       PUM_CUDA(cudaMemcpyAsync(hpq.data(), pq, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
       PUM_CUDA(cudaStreamSynchronize(s));
       bool any = false;
-      for (int c = 0; c < nrhs; ++c) {
-        if (!hlive[c]) continue;
-        PUM_CHECK(hpq[c] > 0.0 && std::isfinite(hrr[c]), PUM_ERR_BREAKDOWN,
-                  "multi-RHS PCG breakdown in column " + std::to_string(c) + " (p^T A p not positive)");
-        const double rel = std::sqrt(hrr[c] / hbb[c]);
-        reps[c].iters = it;
-        reps[c].final_relres = rel;
-        if (reps[c].hist) reps[c].hist[it] = rel;
+      for (int cc = 0; cc < nrhs; ++cc) {
+        if (!hlive[cc]) continue;
+        PUM_CHECK(hpq[cc] > 0.0 && std::isfinite(hrr[cc]), PUM_ERR_BREAKDOWN,
+                  "multi-RHS PCG breakdown in column " + std::to_string(cc) + " (p^T A p not positive)");
+        const double rel = std::sqrt(hrr[cc] / hbb[cc]);
+        reps[cc].iters = it;
+        reps[cc].final_relres = rel;
+        if (reps[cc].hist) reps[cc].hist[it] = rel;
         if (rel <= rtol) {
-          reps[c].converged = 1;
-          hlive[c] = 0;
+          reps[cc].converged = 1;
+          hlive[cc] = 0;
         } else {
           any = true;
         }
@@ -510,7 +616,7 @@ extern "C" pum_status pcg_solve_multi(pum_ctx* ctx, pum_hier* h, int32_t nrhs, c
       if (!any) break;
       PUM_CUDA(cudaMemcpyAsync(live, hlive.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
       if (flexible) PUM_CUDA(cudaMemcpyAsync(zo, z, sizeof(double) * NK, cudaMemcpyDeviceToDevice, s));
-      cycle_block(ctx, h, w, r, z);
+      multi_cycle(ctx, h, c);
       dots(r, z, rzn);
       if (flexible) dots(r, zo, rzc);
       k_pcg_p<<<grid_for(NK), 256, 0, s>>>(p, z, rzn, rzc, rz, live, flexible, N, K);
@@ -524,8 +630,8 @@ extern "C" pum_status pcg_solve_multi(pum_ctx* ctx, pum_hier* h, int32_t nrhs, c
     DevStatus st{};
     PUM_CUDA(cudaMemcpy(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost));
     PUM_CHECK(st.code == 0, (pum_status)st.code, "multi-RHS: device status");
-    for (int c = 0; c < nrhs; ++c)
-      if (!reps[c].converged) return PUM_ERR_NOCONV;
+    for (int cc = 0; cc < nrhs; ++cc)
+      if (!reps[cc].converged) return PUM_ERR_NOCONV;
     return PUM_OK;
   });
 }

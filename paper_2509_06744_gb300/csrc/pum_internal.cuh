@@ -201,6 +201,9 @@ struct GraphCache {
   double* z = nullptr;
 };
 void graph_destroy(GraphCache& g);
+// Work blocks and the captured cycle of the multi-right-hand-side path (multi.cu).
+struct MultiCache;
+void multi_cache_free(MultiCache*& c);
 
 }  // namespace pum
 
@@ -218,6 +221,7 @@ struct pum_hier {
   // more of them for BiCGStab and the convergence factor, allocated on first use
   double* wb[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   pum::GraphCache vgraph;  // captured V-cycle
+  pum::MultiCache* multi = nullptr;  // multi-RHS work blocks and cycle graph (built on first use)
   bool sell = true;        // sliced layouts for the large levels' FP32 products
   bool fused_fsai = true;  // G read once per FSAI application on those levels
 };
