@@ -61,6 +61,9 @@ struct AdaptArgs {
   int* out_np;      // per row: |P_k| (diagonal included)
   int* out_cols;    // per row: np_cap + 1 sorted columns
   double* fmas;     // accumulated FP64 multiply-adds of the algorithm (all rows)
+  double* out_g;    // optional: per row np_cap + 1 blocks of G = L_S^-1 F in ascending column order
+  double* out_f;    // optional: the same blocks of F
+  double* out_ld;   // with out_g: per row log det S_kk
   DevStatus* status;
 };
 
@@ -352,6 +355,13 @@ __global__ void __launch_bounds__(kAdaptThreads) k_adaptive_rows(AdaptArgs a) {
       const int q = s_np;
       const int sq = s_choice;
       if (t == a.t_max - 1) {
+        if (a.out_g && warp == 0) {  // the factor needs the row's state with the last block too
+          warp_replay<D>(a, s_cap, q, s_col[sq], slot(sq), Kr, k, Kr.Z, true, R);
+          double m;
+          int e;
+          if (!warp_chol<D>(Kr.W, Kr.LW, Kr.inv, m, e) && lane == 0) s_fail = 1;
+          if (lane == 0) s_fma += fma_replay<D>(q, true) + fma_chol<D>();
+        }
         if (threadIdx.x == 0) s_np = q + 1;
         __syncthreads();
         break;
@@ -420,6 +430,73 @@ __global__ void __launch_bounds__(kAdaptThreads) k_adaptive_rows(AdaptArgs a) {
       __syncthreads();
       continue;
     }
+    // ---- G and F of the row from the grown factor (Definition 2.2): with L L^T = A[P~,P~] in
+    // the order the blocks joined, Y = L^-T Z_k = A[P~,P~]^-1 A[P~,k], F[k,P~] = -Y^T and
+    // G = L_S^-1 F, written in ascending column order (the diagonal block last)
+    if (a.out_g) {
+      const int np = s_np;
+      int* pos = s_tmp;  // sorted position of the q-th joined block
+      if (threadIdx.x == 0) {
+        for (int q = 0; q < np; ++q) {
+          int r = 0;
+          const int cq = s_col[s_jslot[q]];
+          for (int q2 = 0; q2 < np; ++q2) r += s_col[s_jslot[q2]] < cq;
+          pos[q] = r;
+        }
+      }
+      __syncthreads();
+      double* gout = a.out_g + (int64_t)k * (a.np_cap + 1) * D * D;
+      if (warp == 0) {
+        // backward block substitution: Y_q = L_q^-T (Z_k[q] - sum_{q' > q} Z_{j_q'}[q] Y_q')
+        for (int q = np - 1; q >= 0; --q) {
+          for (int e = lane; e < D * D; e += 32) R[e] = Kr.Z[(int64_t)q * D * D + e];
+          __syncwarp();
+          for (int q2 = q + 1; q2 < np; ++q2) {
+            const double* Zq2 = slot(s_jslot[q2]).Z + (int64_t)q * D * D;  // block (q, q2) of L^T
+            const double* Y2 = gout + (int64_t)pos[q2] * D * D;
+            for (int e = lane; e < D * D; e += 32) {
+              const int r = e / D, c = e - (e / D) * D;
+              double v = R[e];
+#pragma unroll
+              for (int t2 = 0; t2 < D; ++t2) v -= Zq2[r * D + t2] * Y2[t2 * D + c];
+              R[e] = v;
+            }
+            __syncwarp();
+          }
+          const SlotView<D> Lq = slot(s_jslot[q]);
+          warp_ltsolve<D>(Lq.LW, Lq.inv, R);
+          for (int e = lane; e < D * D; e += 32) gout[(int64_t)pos[q] * D * D + e] = R[e];
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      // F = -Y^T and G = L_S^-1 F block by block; the diagonal block F = I, G = L_S^-1
+      for (int q = warp; q <= np; q += kAdaptWarps) {
+        const int pq = q < np ? pos[q] : np;
+        double* gb = gout + (int64_t)pq * D * D;
+        for (int e = lane; e < D * D; e += 32) {
+          const int r = e / D, c = e - (e / D) * D;
+          R[e] = q < np ? -gb[c * D + r] : (r == c ? 1.0 : 0.0);
+        }
+        __syncwarp();
+        if (a.out_f)
+          for (int e = lane; e < D * D; e += 32) a.out_f[((int64_t)k * (a.np_cap + 1) + pq) * D * D + e] = R[e];
+        warp_lsolve<D>(Kr.LW, Kr.inv, R);
+        for (int e = lane; e < D * D; e += 32) gb[e] = R[e];
+        __syncwarp();
+      }
+      if (warp == 0) {
+        double m;
+        int e;
+        warp_chol<D>(Kr.W, X, X + D * D, m, e);  // log det S_kk (S was factored successfully)
+        if (lane == 0) {
+          a.out_ld[k] = log(m) + e * 0.6931471805599453;
+          s_fma += (double)np * (np - 1) / 2.0 * D * D * D + np * 0.5 * D * D * (D - 1) +
+                   (np + 1) * 0.5 * D * D * (D - 1) + fma_chol<D>();
+        }
+      }
+      __syncthreads();
+    }
     // ---- the final pattern P~_k + {k}, ascending
     if (threadIdx.x == 0) {
       const int np = s_np;
@@ -457,6 +534,17 @@ void launch_adapt(pum_ctx* ctx, AdaptArgs& a, int ctas) {
   PUM_CUDA(cudaGetLastError());
 }
 
+// Copy row k's staged blocks (ascending columns) into the BSR's row k.
+__global__ void k_stage_to_bsr(double* __restrict__ dst, int dstride, const double* __restrict__ stage, int cap,
+                               const int* __restrict__ rp, int dd) {
+  const int k = blockIdx.x;
+  const int b0 = rp[k], nb = rp[k + 1] - b0;
+  for (int t = threadIdx.x; t < nb * dd; t += blockDim.x) {
+    const int i = t / dd, e = t - (t / dd) * dd;
+    dst[(int64_t)(b0 + i) * dstride + e] = stage[((int64_t)k * cap + i) * dd + e];
+  }
+}
+
 }  // namespace
 
 // Final patterns of Algorithm 1 for every block row of A (FP64) from the initial pattern P0
@@ -465,7 +553,7 @@ void launch_adapt(pum_ctx* ctx, AdaptArgs& a, int ctas) {
 // instantiation.
 bool adaptive_patterns_device(pum_ctx* ctx, const Bsr& A, const std::vector<std::vector<int>>& P0, int t_max,
                               double tau, double tie_rel, std::vector<std::vector<int>>& rows, double* fp64_flops,
-                              const std::vector<int>* work_rows) {
+                              const std::vector<int>* work_rows, Bsr* G, Bsr* F, double* logdet) {
   const int d = A.d, n = A.n_brows;
   if (d != 3 && d != 6 && d != 10 && d != 15 && d != 21) return false;
   int np0 = 0;
@@ -505,6 +593,17 @@ bool adaptive_patterns_device(pum_ctx* ctx, const Bsr& A, const std::vector<std:
                              ctx->stream));
   }
   a.work = dwork;
+  PUM_CHECK(!G || !work_rows, PUM_ERR_INVALID_ARG, "adaptive FSAI: factors need every row");
+  double *dstage_g = nullptr, *dstage_f = nullptr, *dld = nullptr;
+  if (G) {
+    const size_t sb = sizeof(double) * (size_t)n * (a.np_cap + 1) * d * d;
+    PUM_CUDA(cudaMalloc(&dstage_g, sb));
+    if (F) PUM_CUDA(cudaMalloc(&dstage_f, sb));
+    PUM_CUDA(cudaMalloc(&dld, sizeof(double) * std::max(n, 1)));
+  }
+  a.out_g = dstage_g;
+  a.out_f = dstage_f;
+  a.out_ld = dld;
   double* dfma = nullptr;
   PUM_CUDA(cudaMalloc(&dfma, sizeof(double)));
   PUM_CUDA(cudaMalloc(&dp0rp, sizeof(int) * (n + 1)));
@@ -532,7 +631,6 @@ bool adaptive_patterns_device(pum_ctx* ctx, const Bsr& A, const std::vector<std:
     PUM_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
     PUM_CUDA(cudaMemsetAsync(dfma, 0, sizeof(double), s));
     a.fmas = dfma;
-    timing_begin(ctx, PUM_TK_ADAPT);
     switch (d) {
       case 3: launch_adapt<3>(ctx, a, ctas); break;
       case 6: launch_adapt<6>(ctx, a, ctas); break;
@@ -540,7 +638,6 @@ bool adaptive_patterns_device(pum_ctx* ctx, const Bsr& A, const std::vector<std:
       case 15: launch_adapt<15>(ctx, a, ctas); break;
       default: launch_adapt<21>(ctx, a, ctas); break;
     }
-    timing_end(ctx, PUM_TK_ADAPT);
     PUM_CUDA(cudaStreamSynchronize(s));
     cudaFree(slab);
     PUM_CUDA(cudaMemcpy(&st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost));
@@ -553,8 +650,34 @@ bool adaptive_patterns_device(pum_ctx* ctx, const Bsr& A, const std::vector<std:
     PUM_CUDA(cudaMemcpy(hcols.data(), out_cols, sizeof(int) * hcols.size(), cudaMemcpyDeviceToHost));
     PUM_CUDA(cudaMemcpy(&fma, dfma, sizeof(double), cudaMemcpyDeviceToHost));
   }
+  std::vector<double> hld;
+  if (st.code == 0 && G) {
+    // the factors on the final pattern: BSR allocation, then the staged blocks row by row
+    std::vector<int> rp(n + 1, 0), ci;
+    for (int k = 0; k < n; ++k) {
+      ci.insert(ci.end(), hcols.begin() + (int64_t)k * (a.np_cap + 1),
+                hcols.begin() + (int64_t)k * (a.np_cap + 1) + hnp[k]);
+      rp[k + 1] = (int)ci.size();
+    }
+    bsr_alloc(*G, n, A.n_bcols, d, PUM_F64, rp, ci);
+    if (F) bsr_alloc(*F, n, A.n_bcols, d, PUM_F64, rp, ci);
+    if (n > 0) {
+      k_stage_to_bsr<<<n, 128, 0, s>>>((double*)G->vals, G->stride, dstage_g, a.np_cap + 1, G->row_ptr, d * d);
+      count_launch(ctx);
+      if (F) {
+        k_stage_to_bsr<<<n, 128, 0, s>>>((double*)F->vals, F->stride, dstage_f, a.np_cap + 1, F->row_ptr, d * d);
+        count_launch(ctx);
+      }
+      PUM_CUDA(cudaGetLastError());
+    }
+    hld.resize(n);
+    PUM_CUDA(cudaMemcpy(hld.data(), dld, sizeof(double) * n, cudaMemcpyDeviceToHost));  // waits for the copies
+    double sum = 0.0;
+    for (double v : hld) sum += v;
+    if (logdet) *logdet = sum;
+  }
   for (void* p : {(void*)dp0rp, (void*)dp0ci, (void*)counter, (void*)out_np, (void*)out_cols, (void*)dfma,
-                  (void*)dwork})
+                  (void*)dwork, (void*)dstage_g, (void*)dstage_f, (void*)dld})
     if (p) cudaFree(p);
   if (fp64_flops) *fp64_flops += 2.0 * fma;
   if (st.code != 0)

@@ -561,6 +561,24 @@ std::vector<double> logdet_rows(pum_ctx* ctx, const Bsr& A, const Pattern& P, co
   return out;
 }
 
+// Algorithm 1's pattern (or P0 when not adaptive) and the FSAI factors on it: in one device launch
+// that also forms G (and F) from its grown local factorisations when available, else the pattern
+// search followed by the factor kernel.  Returns sum_k log det S_kk.
+double pattern_and_factor(pum_ctx* ctx, const Bsr& A, const Pattern& P0, const bfsai_params& fp, Pattern& P, Bsr& G,
+                          Bsr* F, Level& L) {
+  if (fp.adaptive && !ctx->adapt_steps) {
+    P = P0;
+    double ld = 0.0;
+    timing_begin(ctx, PUM_TK_ADAPT);
+    const bool done = adaptive_patterns_device(ctx, A, P0.rows, fp.t_max, fp.tau, fp.tie_rel, P.rows, &L.flops_adapt,
+                                               nullptr, &G, F, &ld);
+    timing_end(ctx, PUM_TK_ADAPT);
+    if (done) return ld;
+  }
+  P = fsai_pattern(ctx, A, P0, fp, &L.flops_adapt);
+  return fsai_factor(ctx, A, P, G, F, &L.flops_factor);
+}
+
 constexpr int kLearnedMinRows = 1024;  // smaller levels run Algorithm 1 (cheap there)
 constexpr int kGateStride = 16;        // the gate runs Algorithm 1 on every 16th block row
 constexpr double kGateShortfall = 0.05;
@@ -643,14 +661,14 @@ void fsai_setup_level(pum_ctx* ctx, pum_hier* h, int l) {
   if (!fp.nested) {
     bfsai_params a1 = fp;
     a1.adaptive = fp.adaptive ? 1 : 0;
-    const Pattern P = fsai_pattern(ctx, L.A, P0, a1, &L.flops_adapt);
-    L.logdet_S = fsai_factor(ctx, L.A, P, L.G64, nullptr, &L.flops_factor);
+    Pattern P;
+    L.logdet_S = pattern_and_factor(ctx, L.A, P0, a1, P, L.G64, nullptr, L);
     return;
   }
   // one level of nesting: A1 = F0 A F0^T, inner FSAI of A1 with the same parameters
-  const Pattern Pout = fsai_pattern(ctx, L.A, P0, fp, &L.flops_adapt);
+  Pattern Pout;
   Bsr Gout;
-  fsai_factor(ctx, L.A, Pout, Gout, &L.F064, &L.flops_factor);
+  pattern_and_factor(ctx, L.A, P0, fp, Pout, Gout, &L.F064, L);
   bsr_free(Gout);
   Bsr F0T64, FA;
   bsr_transpose(F0T64, L.F064, s);
@@ -663,8 +681,8 @@ void fsai_setup_level(pum_ctx* ctx, pum_hier* h, int l) {
   // directions fall below the rounding of the triple product); the level then uses the inner
   // block Jacobi, G1 = diag_B(G_outer) = S^{-1/2}, which is the non-nested FSAI (Section 2.2).
   try {
-    const Pattern Pin = fsai_pattern(ctx, L.A1, P0, fp, &L.flops_adapt);
-    L.logdet_S = fsai_factor(ctx, L.A1, Pin, L.G164, nullptr, &L.flops_factor);
+    Pattern Pin;
+    L.logdet_S = pattern_and_factor(ctx, L.A1, P0, fp, Pin, L.G164, nullptr, L);
     L.nested_inner = 1;
   } catch (const Error& e) {
     if (e.st != PUM_ERR_NOT_SPD) throw;

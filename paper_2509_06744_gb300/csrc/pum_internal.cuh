@@ -312,9 +312,12 @@ void mlp_forward_dev(pum_ctx* ctx, const pum_mlp& m, const float* x, int64_t n, 
 // false when the block size has no instantiation.
 // fp64_flops (may be null) accumulates the kernel's FP64 flops (2 per multiply-add).
 // work_rows (may be null): only these rows run Algorithm 1; the others of `rows` keep P0.
+// G (and F) not null: the kernel also forms the FSAI factors of the final patterns from its grown
+// local factorisations (every row; work_rows must be null) and logdet receives sum log det S_kk.
 bool adaptive_patterns_device(pum_ctx* ctx, const Bsr& A, const std::vector<std::vector<int>>& P0, int t_max,
                               double tau, double tie_rel, std::vector<std::vector<int>>& rows, double* fp64_flops,
-                              const std::vector<int>* work_rows = nullptr);
+                              const std::vector<int>* work_rows = nullptr, Bsr* G = nullptr, Bsr* F = nullptr,
+                              double* logdet = nullptr);
 void lanczos_level(pum_ctx* ctx, pum_hier* h, int l);
 void coarse_factor(pum_ctx* ctx, pum_hier* h);
 

@@ -80,4 +80,24 @@ __device__ void warp_lsolve(const double* L, const double* inv, double* X) {
   __syncwarp();
 }
 
+// X (D x D, in place) <- L^-T X for the lower factor L with reciprocal diagonal inv (back
+// substitution with L^T); lanes own columns.
+template <int D>
+__device__ void warp_ltsolve(const double* L, const double* inv, double* X) {
+  const int lane = threadIdx.x & 31;
+  if (lane < D) {
+    double x[D];
+#pragma unroll
+    for (int a = D - 1; a >= 0; --a) {
+      double v = X[a * D + lane];
+#pragma unroll
+      for (int t = a + 1; t < D; ++t) v -= L[t * D + a] * x[t];
+      x[a] = v * inv[a];
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) X[a * D + lane] = x[a];
+  }
+  __syncwarp();
+}
+
 }  // namespace pum

@@ -121,9 +121,12 @@ def test_adaptive_fsai_rows_at_full_size(gpu, exported):
 
 def test_adaptive_fsai_one_launch_equals_step_launches(gpu):
     """Algorithm 1 carried through all steps per row in one launch (incrementally grown local
-    factors) gives, on every level of the 256x256 hierarchy, the patterns of the step-by-step
-    form (every row's local systems factored from scratch each step), bit for bit, and factors
-    within the FSAI tolerance."""
+    factors, from which that launch also forms G) gives, on every level of the 256x256 hierarchy,
+    the patterns of the step-by-step form (every row's local systems factored from scratch each
+    step, G by the factor kernel), bit for bit.  The factors differ by the rounding of the two
+    factorisation orders, amplified by the local condition numbers, which grow on the Galerkin
+    coarse levels (measured: 1.5e-14 of the largest entry on the finest level, 2.1e-10 on level
+    6): 1e-9."""
     import os
     L, ctx, H, b = gpu
     H.setup(p0="lower", adaptive=True, t_max=PR.t_max, tau=PR.tau, k=PR.cheb_k)
@@ -140,7 +143,7 @@ def test_adaptive_fsai_one_launch_equals_step_launches(gpu):
     for l in range(PR.n_levels - 1):
         ref = from_export(H2.export(l, L.PUM_MAT_G))
         assert np.array_equal(one[l].indptr, ref.indptr) and np.array_equal(one[l].indices, ref.indices), l
-        assert np.max(np.abs(one[l].blocks - ref.blocks)) <= TOL_FSAI * np.max(np.abs(ref.blocks))
+        assert np.max(np.abs(one[l].blocks - ref.blocks)) <= 1e-9 * np.max(np.abs(ref.blocks)), l
     H2.close()
     c2.close()
 
