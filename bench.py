@@ -746,6 +746,8 @@ def main():
     n_l, ms_l = kt_live[roof_tk]
     achieved = ab[roof_tk] / (ms_l / n_l * 1e-3) / 1e9
     dom = max(("resid", "g", "gt", "resid64"), key=lambda k: kt[k][1])
+    fused_cfg = [{"level": lv, "rows_per_group": i["gg_rows"], "partitions": i["gg_parts"], "ctas": i["gg_ctas"]}
+                 for lv, i in ((lv, H.info(lv)) for lv in range(pr.n_levels)) if i["fused_fsai"]]
     variants = None
     if not args.no_variants:
         try:  # extra measurements: a failure there must not cost the headline line
@@ -788,6 +790,7 @@ def main():
         "setup_kernels": {k: su64[k] for k in ("adapt", "factor")},
         "setup_roofline": su64["roofline"],
         "kernels_finest": kernels,
+        "fused_fsai_config": fused_cfg,
         "roofline": {"kernel": roof_desc, "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": profiled_traffic(roof_profile, roof_sources),

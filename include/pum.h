@@ -166,6 +166,9 @@ typedef struct {
   int32_t learned;      /* adaptive = 2: 1 when the level kept the learned pattern           */
   double gate;          /* adaptive = 2: the gate's shortfall (see pum_set_pattern_model); -1
                            when the level was not scored by the model                         */
+  int32_t gg_rows, gg_parts, gg_ctas;  /* fused_fsai: the partial-product kernel's configuration
+                           chosen at set-up by timing (block rows per group, consumer partitions
+                           of a group's slots, persistent CTAs); 0 otherwise                  */
 } pum_level_info;
 
 /* Matrices selectable in pum_hier_export. */

@@ -56,7 +56,8 @@ class LevelInfo(C.Structure):
                 ("nnzb_GT", c_int64), ("nnzb_P", c_int64), ("nnzb_F0", c_int64), ("nnzb_G1", c_int64),
                 ("beta", c_double), ("logdet_S", c_double), ("coarsest", c_int32), ("nested_inner", c_int32),
                 ("fused_fsai", c_int32), ("flops_adapt", c_double), ("flops_factor", c_double),
-                ("learned", c_int32), ("gate", c_double)]
+                ("learned", c_int32), ("gate", c_double), ("gg_rows", c_int32), ("gg_parts", c_int32),
+                ("gg_ctas", c_int32)]
 
 
 MLP_FEATURES, MLP_HIDDEN = 12, 64

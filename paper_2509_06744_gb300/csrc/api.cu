@@ -636,6 +636,7 @@ pum_status pum_hier_levels(const pum_hier* h, int* n_levels) {
 pum_status pum_level_info_get(const pum_hier* h, int level, pum_level_info* info) {
   if (!h || !info || level < 0 || level >= (int)h->lv.size()) return PUM_ERR_INVALID_ARG;
   const Level& L = h->lv[level];
+  std::memset(info, 0, sizeof(*info));
   info->m = L.m;
   info->n = L.n;
   info->d = L.d;
@@ -654,6 +655,11 @@ pum_status pum_level_info_get(const pum_hier* h, int level, pum_level_info* info
   info->flops_factor = L.flops_factor;
   info->learned = L.learned;
   info->gate = L.gate;
+  if (L.gg.S.R > 0) {
+    info->gg_rows = L.gg.S.R;
+    info->gg_parts = L.gg.parts;
+    info->gg_ctas = std::min(L.gg.S.n_groups, L.gg.ctas);
+  }
   return PUM_OK;
 }
 

@@ -135,9 +135,10 @@ static void launch_mv_d(pum_ctx* ctx, const Bsr& M, int vdt, const void* x, int 
     return launch_mv_epi<D, float, float, float, float, kAllEpi & ~(1u << EPI_DOT)>(ctx, M, x, epi, e);
   if (mdt == PUM_BF16 && xdt == PUM_F32 && ydt == PUM_F32 && x2dt == PUM_F32)
     return launch_mv_epi<D, __nv_bfloat16, float, float, float, kAllEpi & ~(1u << EPI_DOT)>(ctx, M, x, epi, e);
-  // FP32 smoother accumulating its updates into an FP64 iterate
+  // FP32 smoother accumulating its updates into an FP64 iterate; FP32 restriction with an FP64
+  // copy of its result
   if (mdt == PUM_F32 && xdt == PUM_F32 && ydt == PUM_F32 && x2dt == PUM_F64)
-    return launch_mv_epi<D, float, float, float, double, kChebOnly>(ctx, M, x, epi, e);
+    return launch_mv_epi<D, float, float, float, double, kChebOnly | kSetOnly>(ctx, M, x, epi, e);
   if (mdt == PUM_BF16 && xdt == PUM_F32 && ydt == PUM_F32 && x2dt == PUM_F64)
     return launch_mv_epi<D, __nv_bfloat16, float, float, double, kChebOnly>(ctx, M, x, epi, e);
   // residuals with the FP64 operator and FP64 sums, FP32 result

@@ -317,12 +317,14 @@ __global__ void __launch_bounds__(256) k_gg_gather(int n_brows, const int* __res
   pdl_wait();  // w, and the epilogue's vectors, come from the preceding kernels
   const float* wc = w + c;
   float acc = 0.f;
-  for (int q = q0; q < q1; q += 8) {  // eight independent loads in flight, summed in block order
-    float v[8];
+  // sixteen independent loads in flight (one round for the rows of G^T of the workloads' factors,
+  // 11 blocks on average), summed in block order
+  for (int q = q0; q < q1; q += 16) {
+    float v[16];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = q + u < q1 ? wc[(int64_t)(q + u) * D] : 0.f;
+    for (int u = 0; u < 16; ++u) v[u] = q + u < q1 ? wc[(int64_t)(q + u) * D] : 0.f;
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
+    for (int u = 0; u < 16; ++u)
       if (q + u < q1) acc += v[u];
   }
   pdl_release();

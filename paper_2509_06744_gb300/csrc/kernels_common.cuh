@@ -62,6 +62,7 @@ __device__ __forceinline__ void epilogue(const EpiArgs& e, int64_t tid, AT acc) 
   X2T* x2 = (X2T*)e.xo2;
   if constexpr (EPI == EPI_SET) {
     y[tid] = (YT)acc;
+    if (x2) x2[tid] = (X2T)(YT)acc;  // optional copy of y in the second iterate's precision
   } else if constexpr (EPI == EPI_RESID) {
     // b - A x, formed in the accumulation precision (FP64 for an FP64 operator)
     y[tid] = (YT)((AT)((const XT*)e.b)[tid] - acc);

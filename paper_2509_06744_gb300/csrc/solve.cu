@@ -305,7 +305,9 @@ static void vcycle_mixed(pum_ctx* ctx, pum_hier* h, int l, const double* r, doub
   Level& C = h->lv[l + 1];
   const int tk = l == 0 ? PUM_TK_RESID64 : -1;
   const bool v2k0 = h->sp.cycle == PUM_CYCLE_V2K0;
-  convert_vec(ctx, L.b, PUM_F32, r, PUM_F64, N);  // FP32 right-hand side of the smoother
+  // FP32 right-hand side of the smoother; below the finest level the restriction that produced
+  // r (an FP64 copy of its FP32 result) has already left exactly these values in L.b
+  if (l == 0) convert_vec(ctx, L.b, PUM_F32, r, PUM_F64, N);
   // pre-smoothing: z = e in FP64 (k steps, 2k for V(2k,0))
   cheb4(ctx, h, l, L.b, L.e, true, z, PUM_F64, true, L.zs, v2k0 ? 2 * h->sp.degree_k : 0);
   EpiArgs er{};
@@ -325,9 +327,9 @@ static void vcycle_mixed(pum_ctx* ctx, pum_hier* h, int l, const double* r, doub
     pa.ys = L.zs;
     bsr_mv(ctx, L.P, PUM_F64, C.x, EPI_ADD, pa);  // z += P x_c (FP64)
   } else if (is_mixed(h, l + 1) || l + 1 == (int)h->lv.size() - 1) {
+    rs.xo2 = C.b64;  // and its FP64 copy, the coarser level's right-hand side
+    rs.x2dt = PUM_F64;
     bsr_mv(ctx, L.PTs, PUM_F32, L.r, EPI_SET, rs);  // b_c = P^T r_f
-    const int64_t Nc = (int64_t)C.n * C.d;
-    convert_vec(ctx, C.b64, PUM_F64, C.b, PUM_F32, Nc);
     vcycle_mixed(ctx, h, l + 1, C.b64, C.z64);
     pa.y = z;
     pa.ys = L.zs;

@@ -132,6 +132,8 @@ def test_learned_setup_passes_gate_and_matches_selection(lib, ctx, trained):
     H.setup(p0="lower", adaptive=True, t_max=6, k=3)
     x = torch.zeros_like(b)
     ref = H.pcg(b, x, rtol=1e-8, maxit=100)
+    e0 = torch.tensor(pin.uniform_vector(b.numel(), 5), dtype=torch.float64, device="cuda")
+    rho_ref = H.convergence_factor(e0, 6)
     cand = H.candidates(0)
     ctx.set_pattern_model(model)
     H.setup(p0="lower", adaptive=2, t_max=6, k=3)
@@ -148,6 +150,9 @@ def test_learned_setup_passes_gate_and_matches_selection(lib, ctx, trained):
     x = torch.zeros_like(b)
     rep = H.pcg(b, x, rtol=1e-8, maxit=100)
     assert rep["converged"] and rep["iters"] <= ref["iters"] + 1
+    # the other half of the acceptance rule: the V-cycle's convergence factor within 5% of the
+    # one with Algorithm 1's patterns (the set-up's gate measures the Kaporin half per level)
+    assert H.convergence_factor(e0, 6) <= 1.05 * rho_ref
     ctx.set_pattern_model(None)
     H.close()
 
