@@ -25,7 +25,6 @@ __global__ void __launch_bounds__(256) k_bsr_mv(int n_brows, int stride, int lan
                                                 const int* __restrict__ ci, const MT* __restrict__ vals,
                                                 const XT* __restrict__ x, EpiArgs e) {
   using AT = typename AccOf<MT>::type;
-  pdl_wait();
   const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t tid = gtid / lanes;  // output unknown
   const int g = (int)(gtid - tid * lanes);
@@ -33,18 +32,49 @@ __global__ void __launch_bounds__(256) k_bsr_mv(int n_brows, int stride, int lan
   const int r = (int)(tid - (int64_t)row * D);
   const bool active = row < n_brows;
   AT acc = 0;
-  if (active) {
-    const int b0 = rp[row], b1 = rp[row + 1];
-    for (int b = b0 + g; b < b1; b += lanes) {
-      const int c = __ldg(ci + b);
-      AT a[D], xv[D];
-      load_row<D>(vals + (int64_t)b * stride + r * D, a);
+  if constexpr (kEarlyTrigger<D>) {
+    // The matrix does not change while products run (no kernel that writes one triggers its
+    // dependents early), so the row's extent and this lane's first block (its column and matrix
+    // row) are loaded before waiting for the preceding kernel: on the small coarse levels, where
+    // each lane has one or two blocks, that takes two of the three dependent loads off the chain.
+    int b = 0, b1 = 0, c = 0;
+    AT a[D];
+    if (active) {
+      b = __ldg(rp + row) + g;
+      b1 = __ldg(rp + row + 1);
+      if (b < b1) {
+        c = __ldg(ci + b);
+        load_row<D>(vals + (int64_t)b * stride + r * D, a);
+      }
+    }
+    pdl_wait();
+    pdl_release();  // the next kernel may launch and issue its own pre-wait loads
+    while (b < b1) {
+      AT xv[D];
       load_row<D>(x + (int64_t)c * D, xv);
 #pragma unroll
       for (int q = 0; q < D; ++q) acc = fma(a[q], xv[q], acc);
+      b += lanes;
+      if (b < b1) {
+        c = __ldg(ci + b);
+        load_row<D>(vals + (int64_t)b * stride + r * D, a);
+      }
     }
+  } else {
+    pdl_wait();
+    if (active) {
+      const int b1 = rp[row + 1];
+      for (int b = rp[row] + g; b < b1; b += lanes) {
+        const int c = __ldg(ci + b);
+        AT a[D], xv[D];
+        load_row<D>(vals + (int64_t)b * stride + r * D, a);
+        load_row<D>(x + (int64_t)c * D, xv);
+#pragma unroll
+        for (int q = 0; q < D; ++q) acc = fma(a[q], xv[q], acc);
+      }
+    }
+    pdl_release();
   }
-  pdl_release();
   for (int o = lanes >> 1; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o, lanes);
   const bool leader = active && g == 0;
   if constexpr (EPI == EPI_DOT) {

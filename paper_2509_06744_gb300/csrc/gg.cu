@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(kGgMaxThreads) k_gg_partial(int n_groups, int 
 
   // Consumers: P partitions of RDp threads (RD rounded up to whole warps); partition p takes the
   // slots s = p, p + P, ... of the group.
+  if constexpr (kEarlyTrigger<D>) pdl_release();  // the gather may launch; it waits for this kernel
   const int nct = (int)blockDim.x - 32;
   const int RDp = (RD + 31) / 32 * 32;
   const int P = nct / RDp;
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(kGgMaxThreads) k_gg_partial(int n_groups, int 
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(empty + b);  // this warp is done with buffer b
   }
-  pdl_release();
+  if constexpr (!kEarlyTrigger<D>) pdl_release();
 }
 
 template <int D, typename YT, typename X2T, int EPI>
@@ -315,6 +316,7 @@ __global__ void __launch_bounds__(256) k_gg_gather(int n_brows, const int* __res
     q1 = __ldg(tptr + i + 1);
   }
   pdl_wait();  // w, and the epilogue's vectors, come from the preceding kernels
+  if constexpr (kEarlyTrigger<D>) pdl_release();  // the next kernel may launch and issue its pre-wait loads
   const float* wc = w + c;
   float acc = 0.f;
   // sixteen independent loads in flight (one round for the rows of G^T of the workloads' factors,
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(256) k_gg_gather(int n_brows, const int* __res
     for (int u = 0; u < 16; ++u)
       if (q + u < q1) acc += v[u];
   }
-  pdl_release();
+  if constexpr (!kEarlyTrigger<D>) pdl_release();
   if (live) epilogue<EPI, float, float, YT, X2T>(e, u, acc);
 }
 

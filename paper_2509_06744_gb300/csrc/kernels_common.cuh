@@ -11,8 +11,18 @@ namespace pum {
 // predecessor has completed and its writes are visible (every thread that touches memory the
 // predecessor writes, or that later kernels read through this one, passes it first), and
 // pdl_release() lets the successor start launching.  Both are no-ops for ordinary launches.
+// Before its own wait a kernel touches only constant data (matrix structure and values); no
+// kernel that writes a matrix triggers early, so a matrix read before the wait is complete.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Products of block size D <= 10 trigger right after their own wait, so that the successor
+// becomes resident early and issues its constant loads while they run (measured on the 256^2
+// biharmonic solve, d = 10: 10.15 -> 9.6 ms, most of it on the small levels).  With d = 21 the
+// same placement made the triharmonic solves slower (by 3% to 24% across the variants tried),
+// so larger blocks trigger after their main loop, as before.
+template <int D>
+constexpr bool kEarlyTrigger = D <= 10;
 
 template <typename T> struct AccOf { using type = float; };
 template <> struct AccOf<double> { using type = double; };

@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(kSellMaxThreads) k_sell_mv(int n_brows, int R,
   float sh = 0.f, sl = 0.f, sc = 0.f;  // double-float accumulator (kDF)
   XV xn[D];
   pdl_wait();  // x and the epilogue's vectors come from the preceding kernel (the matrix does not)
+  if constexpr (kEarlyTrigger<D>) pdl_release();  // the next kernel may launch and issue its pre-wait loads
   auto load_x = [&](int c, XV(&out)[D]) {
     if constexpr (kDF)
       load_row_df<D>(reinterpret_cast<const float2*>(x) + (int64_t)c * D, out);
@@ -164,7 +165,7 @@ __global__ void __launch_bounds__(kSellMaxThreads) k_sell_mv(int n_brows, int R,
     __syncwarp();
     if ((threadIdx.x & 31) == 0) mbar_arrive(empty + k);
   }
-  pdl_release();
+  if constexpr (!kEarlyTrigger<D>) pdl_release();
   const int row = g * R + j;
   if (!(computes && row < n_brows)) return;
   if constexpr (kDF) {
