@@ -593,6 +593,12 @@ def test_fused_fsai_application_matches_two_products(lib, d, side, g, nested):
         c.sync()  # raises on a device status (a bounded wait that expired)
         mats = [from_export(H.export(0, w)) for w in ((lib.PUM_MAT_F0, lib.PUM_MAT_G1) if nested else (lib.PUM_MAT_G,))]
         outs[fused] = (host(z), host(z2), host(x), mats)
+        info = H.info(0)  # the configuration the set-up's timing chose, reported only when fused
+        cfg = (info["gg_rows"], info["gg_parts"], info["gg_ctas"])
+        if info["fused_fsai"]:
+            assert fused and cfg[0] >= 2 and 1 <= cfg[1] <= 4 and cfg[2] >= 1
+        else:
+            assert cfg == (0, 0, 0)
         H.close()
         c.close()
     zf, zf2, xf, mats = outs[True]
