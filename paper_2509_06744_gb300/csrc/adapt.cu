@@ -172,8 +172,89 @@ __device__ double warp_score(const SlotView<D>& Kr, const SlotView<D>& C, double
   return ldexp(mx / mw, ex - ew);
 }
 
+// Scores of small blocks (D <= 10) are split in two passes so that the two d x d Cholesky
+// factorisations of a score run one candidate per thread instead of one matrix per warp (whose
+// pivots and shrinking trailing triangles leave most lanes idle): first, per candidate and by one
+// warp, X = W_c - U^T U with U = L_S^{-1} H_kc, stored in the candidate's LW area; then, per
+// candidate and by one thread, det X and chol(W_c) into LW (kept for the candidate's possible
+// joining) and rho_c = det X / det W_c.  The per-thread factorisation performs the operations of
+// warp_chol in the same order for every element, so the scores are the same bit for bit.
 template <int D>
-__global__ void __launch_bounds__(kAdaptThreads) k_adaptive_rows(AdaptArgs a) {
+constexpr bool kThreadChol = D <= 10;
+
+template <int D>
+__device__ void warp_score_x(const SlotView<D>& Kr, const SlotView<D>& C, double* R) {
+  const int lane = threadIdx.x & 31;
+  for (int e = lane; e < D * D; e += 32) R[e] = C.H[e];
+  __syncwarp();
+  warp_lsolve<D>(Kr.LW, Kr.inv, R);
+  for (int e = lane; e < D * D; e += 32) {
+    const int r = e / D, c = e - (e / D) * D;
+    double v = C.W[e];
+#pragma unroll
+    for (int t = 0; t < D; ++t) v -= R[t * D + r] * R[t * D + c];
+    C.LW[e] = v;
+  }
+  __syncwarp();
+}
+
+// Cholesky of the symmetric D x D matrix src (row-major, lower part read) by one thread, with the
+// element operations of warp_chol in its order; the lower factor into dst and the reciprocal
+// diagonal into inv when given.  det = mant * 2^expo.  False when a pivot is not positive.
+template <int D>
+__device__ bool thread_chol(const double* src, double* dst, double* inv, double& mant, int& expo) {
+  double m[D * (D + 1) / 2];  // packed lower triangle: (i, c) at i (i + 1) / 2 + c
+#pragma unroll
+  for (int i = 0; i < D; ++i)
+#pragma unroll
+    for (int c = 0; c <= i; ++c) m[i * (i + 1) / 2 + c] = src[i * D + c];
+  mant = 1.0;
+  expo = 0;
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const double piv = m[j * (j + 1) / 2 + j];
+    if (!(piv > 0.0)) {
+      ok = false;
+      break;
+    }
+    const double l = sqrt(piv);
+    const double il = 1.0 / l;
+    int ex = 0;
+    mant = frexp(mant * piv, &ex);
+    expo += ex;
+    m[j * (j + 1) / 2 + j] = l;
+    if (inv) inv[j] = il;
+#pragma unroll
+    for (int i = j + 1; i < D; ++i) m[i * (i + 1) / 2 + j] *= il;
+#pragma unroll
+    for (int i = j + 1; i < D; ++i)
+#pragma unroll
+      for (int c = j + 1; c <= i; ++c) m[i * (i + 1) / 2 + c] -= m[i * (i + 1) / 2 + j] * m[c * (c + 1) / 2 + j];
+  }
+  if (dst)
+#pragma unroll
+    for (int i = 0; i < D; ++i)
+#pragma unroll
+      for (int c = 0; c <= i; ++c) dst[i * D + c] = m[i * (i + 1) / 2 + c];
+  return ok;
+}
+
+// rho_c from X (in C.LW, left by warp_score_x) and W_c, one thread; chol(W_c) into C.LW / C.inv.
+template <int D>
+__device__ double thread_score(const SlotView<D>& C) {
+  double mx, mw;
+  int ex, ew;
+  const bool okx = thread_chol<D>(C.LW, nullptr, nullptr, mx, ex);
+  const bool okw = thread_chol<D>(C.W, C.LW, C.inv, mw, ew);
+  if (!okx || !okw) return -1.0;
+  return ldexp(mx / mw, ex - ew);
+}
+
+// Four CTAs per SM (the launch's CTA count): the register cap spills a little of the d = 10
+// per-thread Cholesky, which measured faster than three CTAs per SM without spills.
+template <int D>
+__global__ void __launch_bounds__(kAdaptThreads, 4) k_adaptive_rows(AdaptArgs a) {
   extern __shared__ double sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s_cap = a.np_cap * D;
@@ -319,10 +400,18 @@ __global__ void __launch_bounds__(kAdaptThreads) k_adaptive_rows(AdaptArgs a) {
       for (int q = 0; q < s_np; ++q) s_fma += (s_nslot - 1 - s_np0) * fma_replay<D>(q, false);
     // ---- the steps of Algorithm 1
     for (int t = 0; t < a.t_max; ++t) {
-      for (int s = warp; s < s_nslot; s += kAdaptWarps) {
-        if (s_state[s] != 2) continue;
-        const double rho = warp_score<D>(Kr, slot(s), R, X);
-        if (lane == 0) s_rho[s] = rho;
+      if constexpr (kThreadChol<D>) {
+        for (int s = warp; s < s_nslot; s += kAdaptWarps)
+          if (s_state[s] == 2) warp_score_x<D>(Kr, slot(s), R);
+        __syncthreads();
+        for (int s = threadIdx.x; s < s_nslot; s += kAdaptThreads)
+          if (s_state[s] == 2) s_rho[s] = thread_score<D>(slot(s));
+      } else {
+        for (int s = warp; s < s_nslot; s += kAdaptWarps) {
+          if (s_state[s] != 2) continue;
+          const double rho = warp_score<D>(Kr, slot(s), R, X);
+          if (lane == 0) s_rho[s] = rho;
+        }
       }
       __syncthreads();
       if (threadIdx.x == 0) {
