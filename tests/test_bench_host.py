@@ -84,3 +84,23 @@ def test_oracle_sample_is_observed_at_its_own_size():
     assert o["m"] == 8 and o["n_levels"] == 4 and o["unknowns"] == 640
     assert len(o["solve_ms"]) == 2 and all(t > 0 for t in o["solve_ms"])
     assert 0 < o["iters"] < 50 and o["hierarchy_s"] > 0 and o["smoother_setup_s"] > 0
+
+
+def test_profiled_traffic_only_for_the_captured_sources(tmp_path, monkeypatch):
+    """The roofline line carries the ncu DRAM bytes of its kernel only while the kernel's sources
+    hash to the value recorded with the capture; a changed source (or no summary) gives None."""
+    import hashlib
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1\n")
+    digest = hashlib.sha256(src.read_bytes()).hexdigest()
+    prof = tmp_path / "p.md"
+    prof.write_text(f"traffic_bytes_per_launch: 303114752\nkernel_source_sha256: {digest}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("p.md", ("k.cu",)) == 303114752
+    assert bench.profiled_traffic(None, ("k.cu",)) is None
+    src.write_text("kernel v2\n")
+    assert bench.profiled_traffic("p.md", ("k.cu",)) is None
+    # the committed summary matches the committed sources of the fused kernel
+    monkeypatch.undo()
+    _, _, profile, sources = bench.ROOFLINE[True]
+    assert bench.profiled_traffic(profile, sources) is not None, f"{profile} was captured from other sources"
