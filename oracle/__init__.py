@@ -12,6 +12,11 @@ Modules:
     pum     Section 4 / Example 5.1 / Example 5.4: cover, partition of unity,
             local Legendre spaces, Nitsche forms, load vector, mass matrix,
             L2-projection prolongation and Galerkin coarse operators.
+    pum3d   Example 5.3: the same construction on the unit cube for the biharmonic
+            equation (Nitsche face terms, projection, prolongation, hierarchy).
+    learned Candidate pools, features, labels and the scoring network of the
+            learned adaptive pattern (not a method of the paper; Algorithm 1 is its
+            teacher and judge).
     blocks  Definition 2.1: block-sparse matrices and their patterns.
     fsai    Definition 2.2, Lemma 2.7, Algorithm 1 and Section 2.2: block-FSAI
             (static, adaptive, nested) and the Kaporin-type measure.
