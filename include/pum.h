@@ -207,7 +207,11 @@ pum_status pum_assemble(pum_ctx *ctx, const pum_problem *prob, pum_hier **out, d
 /* Build a hierarchy from caller matrices (copied; caller keeps ownership).  A[0] is the
  * finest operator; for l >= 1, A[l] with vals == NULL is computed as P[l-1]^T A[l-1] P[l-1].
  * P[l] (l = 0..n_levels-2) maps level l+1 to level l (n_brows = n_l, n_bcols = n_{l+1}).
- * All blocks must share one bs <= 32.  Synchronous. */
+ * All blocks must share one block size: 3, 6, 10, 15 or 21 (the square's local spaces,
+ * p = 1..5) or 20 (the cube's, p = 3: Example 5.3, whose matrices the caller assembles; the
+ * library assembles the square only).  With 20 every level runs on the block-row kernels (no
+ * sliced or fused layouts) and the learned pattern and multi-RHS products are not available.
+ * Synchronous. */
 pum_status pum_hier_from_bsr(pum_ctx *ctx, int n_levels, const pum_bsr_view *A, const pum_bsr_view *P,
                              pum_hier **out);
 

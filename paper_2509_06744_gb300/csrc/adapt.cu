@@ -644,7 +644,7 @@ bool adaptive_patterns_device(pum_ctx* ctx, const Bsr& A, const std::vector<std:
                               double tau, double tie_rel, std::vector<std::vector<int>>& rows, double* fp64_flops,
                               const std::vector<int>* work_rows, Bsr* G, Bsr* F, double* logdet) {
   const int d = A.d, n = A.n_brows;
-  if (d != 3 && d != 6 && d != 10 && d != 15 && d != 21) return false;
+  if (d != 3 && d != 6 && d != 10 && d != 15 && d != 20 && d != 21) return false;
   int np0 = 0;
   std::vector<int> p0rp(n + 1, 0), p0ci;
   for (int i = 0; i < n; ++i) {
@@ -725,7 +725,9 @@ bool adaptive_patterns_device(pum_ctx* ctx, const Bsr& A, const std::vector<std:
       case 6: launch_adapt<6>(ctx, a, ctas); break;
       case 10: launch_adapt<10>(ctx, a, ctas); break;
       case 15: launch_adapt<15>(ctx, a, ctas); break;
-      default: launch_adapt<21>(ctx, a, ctas); break;
+      case 20: launch_adapt<20>(ctx, a, ctas); break;
+      case 21: launch_adapt<21>(ctx, a, ctas); break;
+      default: PUM_CHECK(false, PUM_ERR_UNSUPPORTED, "Algorithm 1: unsupported block size");
     }
     PUM_CUDA(cudaStreamSynchronize(s));
     cudaFree(slab);

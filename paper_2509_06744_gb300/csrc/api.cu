@@ -46,7 +46,8 @@ pum_status guard(pum_ctx* ctx, F&& f) {
   }
 }
 
-bool is_supported_bs(int d) { return d == 3 || d == 6 || d == 10 || d == 15 || d == 21; }
+// binom(p+2, 2) for p = 1..5 (the square's local spaces) and 20 = binom(6, 3) (the cube's, p = 3)
+bool is_supported_bs(int d) { return d == 3 || d == 6 || d == 10 || d == 15 || d == 20 || d == 21; }
 
 void check_vec(const void* p, const char* name) {
   PUM_CHECK(p != nullptr, PUM_ERR_INVALID_ARG, std::string(name) + " is NULL");

@@ -198,8 +198,9 @@ void bsr_mv(pum_ctx* ctx, const Bsr& M, int vdt, const void* x, int epi, const E
     case 6: launch_mv_d<6>(ctx, M, vdt, x, epi, e); break;
     case 10: launch_mv_d<10>(ctx, M, vdt, x, epi, e); break;
     case 15: launch_mv_d<15>(ctx, M, vdt, x, epi, e); break;
+    case 20: launch_mv_d<20>(ctx, M, vdt, x, epi, e); break;
     case 21: launch_mv_d<21>(ctx, M, vdt, x, epi, e); break;
-    default: throw Error{PUM_ERR_UNSUPPORTED, "block size must be (p+1)(p+2)/2 with p = 1..5"};
+    default: throw Error{PUM_ERR_UNSUPPORTED, "block size must be 3, 6, 10, 15, 21 (square) or 20 (cube)"};
   }
   if (tk >= 0) timing_end(ctx, tk);
 }

@@ -504,7 +504,8 @@ void candidates_build(pum_ctx* ctx, const Bsr& A, const Bsr& G0, const std::vect
     case 6: diag_launch<6>(ctx, A, nrm, Ld, invd); gain_launch<6>(ctx, A, G0, cs, nrm, Ld, invd, gain, akc); break;
     case 10: diag_launch<10>(ctx, A, nrm, Ld, invd); gain_launch<10>(ctx, A, G0, cs, nrm, Ld, invd, gain, akc); break;
     case 15: diag_launch<15>(ctx, A, nrm, Ld, invd); gain_launch<15>(ctx, A, G0, cs, nrm, Ld, invd, gain, akc); break;
-    default: diag_launch<21>(ctx, A, nrm, Ld, invd); gain_launch<21>(ctx, A, G0, cs, nrm, Ld, invd, gain, akc); break;
+    case 21: diag_launch<21>(ctx, A, nrm, Ld, invd); gain_launch<21>(ctx, A, G0, cs, nrm, Ld, invd, gain, akc); break;
+    default: throw Error{PUM_ERR_UNSUPPORTED, "learned candidates: unsupported block size"};
   }
   k_cand_feat<<<(unsigned)((n + kWarps - 1) / kWarps), kWarps * 32, 0, s>>>(
       A.row_ptr, A.col_idx, (const double*)A.vals, A.stride, d, n, m, std::max(A.max_row_nnzb, 1), d_prp, d_pci,

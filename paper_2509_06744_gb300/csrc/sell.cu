@@ -343,7 +343,8 @@ static int sell_occupancy_for(int d, int kind, int R, int max_slots) {
     case 6: return sell_occupancy_d<6>(kind, R, max_slots);
     case 10: return sell_occupancy_d<10>(kind, R, max_slots);
     case 15: return sell_occupancy_d<15>(kind, R, max_slots);
-    default: return sell_occupancy_d<21>(kind, R, max_slots);
+    case 21: return sell_occupancy_d<21>(kind, R, max_slots);
+    default: throw Error{PUM_ERR_UNSUPPORTED, "sliced layout: unsupported block size"};
   }
 }
 

@@ -498,9 +498,10 @@ def _random_block_spd(n_side, d, seed):
     return bk.from_blocks(n, n, d, ent)
 
 
-@pytest.mark.parametrize("d", [3, 6, 10, 15, 21])
+@pytest.mark.parametrize("d", [3, 6, 10, 15, 20, 21])
 def test_block_sizes_residual_and_static_fsai(lib, ctx, d):
-    """Every supported block size, with a row count that leaves a ragged last thread block."""
+    """Every supported block size (20: the cube's p = 3), with a row count that leaves a ragged
+    last thread block."""
     A = _random_block_spd(5, d, seed=d)
     H = lib.Hierarchy.from_bsr(ctx, [to_view(A)], [])
     N = A.n_rows * d
