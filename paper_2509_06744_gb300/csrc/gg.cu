@@ -354,8 +354,7 @@ int gg_occupancy_for(int d, int dt, int R, int P, int ns_max) {
     case 6: return gg_occupancy_d<6>(dt, R, P, ns_max);
     case 10: return gg_occupancy_d<10>(dt, R, P, ns_max);
     case 15: return gg_occupancy_d<15>(dt, R, P, ns_max);
-    case 21: return gg_occupancy_d<21>(dt, R, P, ns_max);
-    default: throw Error{PUM_ERR_UNSUPPORTED, "fused FSAI layout: unsupported block size"};
+    default: return gg_occupancy_d<21>(dt, R, P, ns_max);
   }
 }
 
@@ -538,8 +537,7 @@ float gg_time_partial(pum_ctx* ctx, const FusedG& F, const float* x, int reps) {
       case 6: gg_partial_launch_dt<6>(ctx, F, x); break;
       case 10: gg_partial_launch_dt<10>(ctx, F, x); break;
       case 15: gg_partial_launch_dt<15>(ctx, F, x); break;
-      case 21: gg_partial_launch_dt<21>(ctx, F, x); break;
-      default: throw Error{PUM_ERR_UNSUPPORTED, "fused FSAI layout: unsupported block size"};
+      default: gg_partial_launch_dt<21>(ctx, F, x); break;
     }
   };
   cudaEvent_t a, b;
