@@ -14,6 +14,8 @@ Modules:
             L2-projection prolongation and Galerkin coarse operators.
     pum3d   Example 5.3: the same construction on the unit cube for the biharmonic
             equation (Nitsche face terms, projection, prolongation, hierarchy).
+    pum_raise  Example 5.1's space with the degree raised on boundary patches
+            (variable local dimension; assembly, projection, prolongation).
     learned Candidate pools, features, labels and the scoring network of the
             learned adaptive pattern (not a method of the paper; Algorithm 1 is its
             teacher and judge).
