@@ -178,6 +178,19 @@ def local_projection(m: int, p: int, p_boundary: int, func, q: int = 12) -> np.n
 
 
 def prolongation(m_f: int, p: int, p_boundary: int, q: int | None = None) -> sps.csr_matrix:
+    """P of prolongation_blocks as a CSR matrix over the scalar unknowns."""
+    blocks, off_f, off_c = prolongation_blocks(m_f, p, p_boundary, q)
+    rows, cols, vals = [], [], []
+    for (i, j), B in blocks.items():
+        r, c = np.meshgrid(np.arange(off_f[i], off_f[i + 1]), np.arange(off_c[j], off_c[j + 1]), indexing="ij")
+        rows.append(r.ravel())
+        cols.append(c.ravel())
+        vals.append(B.ravel())
+    return sps.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(int(off_f[-1]), int(off_c[-1])))
+
+
+def prolongation_blocks(m_f: int, p: int, p_boundary: int, q: int | None = None):
     """P from the raised space of level m_f / 2 to that of level m_f by global-to-local L2
     projection (Section 4): block (i, j) = M_i^{-1} B_ij with M_i the fine local mass matrix and
     B_ij the integral of fine basis i against coarse basis function j (PU times its local
@@ -224,11 +237,72 @@ def prolongation(m_f: int, p: int, p_boundary: int, q: int | None = None) -> sps
                             Bs[j] = Bs.get(j, 0.0) + (th * W) @ psi.T
             for j, B in Bs.items():
                 blocks[(i, j)] = np.linalg.solve(Mi, B)
-    rows, cols, vals = [], [], []
-    for (i, j), B in blocks.items():
-        r, c = np.meshgrid(np.arange(off_f[i], off_f[i + 1]), np.arange(off_c[j], off_c[j + 1]), indexing="ij")
-        rows.append(r.ravel())
-        cols.append(c.ravel())
-        vals.append(B.ravel())
-    return sps.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                          shape=(int(off_f[-1]), int(off_c[-1])))
+    return blocks, off_f, off_c
+
+
+# ---------------------------------------------------------------------------
+# The raised space on a uniform block layout (padding)
+# ---------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class PaddedHierarchy:
+    """Levels finest first, every block d_pad x d_pad: A[l] and P[l] as BlockCSR, the load vector
+    b on the padded unknowns, and per level the indices of the real (unpadded) unknowns."""
+    m: list
+    A: list
+    P: list
+    b: np.ndarray
+    real: list
+    A_raised: sps.csr_matrix  # the finest raised operator, unpadded
+    b_raised: np.ndarray
+
+
+def _pad_csr(M: sps.csr_matrix, off_r: np.ndarray, off_c: np.ndarray, d: int, identity: bool) -> dict:
+    """Blocks of M (variable sizes by offsets) embedded top-left in d x d blocks; with identity,
+    the padded diagonal entries of the diagonal blocks are 1 (decoupled padded unknowns)."""
+    M = M.tocsr()
+    nr, nc = len(off_r) - 1, len(off_c) - 1
+    rb = np.searchsorted(off_r, np.arange(off_r[-1]), side="right") - 1
+    cb = np.searchsorted(off_c, np.arange(off_c[-1]), side="right") - 1
+    coo = M.tocoo()
+    out = {}
+    for r, c, v in zip(coo.row, coo.col, coo.data):
+        i, j = int(rb[r]), int(cb[c])
+        if (i, j) not in out:
+            out[(i, j)] = np.zeros((d, d))
+        out[(i, j)][r - off_r[i], c - off_c[j]] += v
+    if identity:
+        assert nr == nc
+        for i in range(nr):
+            B = out.setdefault((i, i), np.zeros((d, d)))
+            for t in range(off_r[i + 1] - off_r[i], d):
+                B[t, t] = 1.0
+    return out
+
+
+def padded_hierarchy(m: int, p: int, p_boundary: int, n_levels: int, f=None) -> PaddedHierarchy:
+    """The raised space's Galerkin hierarchy (finest assembly, L2-projection prolongations,
+    A_{l-1} = P^T A_l P on the unpadded unknowns), each level written with uniform blocks of the
+    raised dimension: padded unknowns carry an identity diagonal and no coupling, so they stay
+    zero in every product and the padded system's solution restricted to the real unknowns is
+    the raised one."""
+    from . import blocks as bk
+    d = local_dim(max(p, p_boundary))
+    asm = assemble(m, p, p_boundary, f=f)
+    A, off = asm.A, asm.off
+    ms, As, Ps, reals = [m], [], [], []
+    A_l, off_l, m_l = A, off, m
+    for lev in range(n_levels):
+        As.append(bk.from_blocks(m_l * m_l, m_l * m_l, d, _pad_csr(A_l, off_l, off_l, d, True)))
+        reals.append(np.concatenate([np.arange(i * d, i * d + off_l[i + 1] - off_l[i]) for i in range(m_l * m_l)]))
+        if lev == n_levels - 1:
+            break
+        Pb, off_f, off_c = prolongation_blocks(m_l, p, p_boundary)
+        Pm = prolongation(m_l, p, p_boundary)
+        Ps.append(bk.from_blocks(m_l * m_l, (m_l // 2) ** 2, d, _pad_csr(Pm, off_f, off_c, d, False)))
+        A_l = (Pm.T @ A_l @ Pm).tocsr()
+        off_l, m_l = off_c, m_l // 2
+        ms.append(m_l)
+    b = np.zeros(m * m * d)
+    b[reals[0]] = asm.b
+    return PaddedHierarchy(ms, As, Ps, b, reals, A, asm.b)

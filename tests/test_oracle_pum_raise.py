@@ -98,3 +98,18 @@ def test_raised_prolongation_reproduces_quadratics_and_galerkin_is_spd(m_f):
     Ac = (Pm.T @ A @ Pm).toarray()
     assert np.max(np.abs(Ac - Ac.T)) <= 1e-12 * np.max(np.abs(Ac))
     assert np.min(np.linalg.eigvalsh(Ac)) > 0.0
+
+
+def test_padded_layout_solves_the_raised_system():
+    """The raised space on uniform 10 x 10 blocks (interior patches padded with decoupled unknowns
+    of unit diagonal): the multilevel PCG on the padded hierarchy keeps every padded unknown at
+    zero and its real unknowns solve the raised system."""
+    import scipy.sparse.linalg as spla
+    from oracle import solver
+    h = pum_raise.padded_hierarchy(8, 2, 3, 3, f=lambda x, y: np.sin(np.pi * x) * np.sin(np.pi * y) + 0.5)
+    assert [A.n_rows for A in h.A] == [64, 16, 4] and h.A[0].d == 10
+    xr = spla.spsolve(h.A_raised.tocsc(), h.b_raised)
+    res = solver.solve(solver.build_setup(h, k=2, mode="adaptive", P0="lower", t_max=3), h.b, rtol=1e-10)
+    pad = np.setdiff1d(np.arange(len(h.b)), h.real[0])
+    assert res.converged and np.all(res.x[pad] == 0.0)
+    assert np.linalg.norm(res.x[h.real[0]] - xr) <= 1e-9 * np.linalg.norm(xr)
